@@ -1,0 +1,361 @@
+"""Benchmark of the Sec. 5 pipeline out = Re(ifft2(H . fft2(img))) on GB300.
+
+Workload: one 4096 x 4096 float32 synthetic sky per step (background 100,
+Gaussian noise sigma 10, 20000 Gaussian-PSF sources of sigma 1.5 px with
+log-uniform peak amplitudes 10..1e4, seeded) through a Butterworth low-pass
+(order 4, cutoff 0.1 x Nyquist).  It stands in for the paper's galaxy image.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gbfft|reference]
+
+Prints one JSON line (rank 0).  `value` is the pipeline's throughput
+expressed as the bandwidth of its compulsory I/O: 12 bytes per pixel (read
+img and H, write out) divided by the device time per image.  Each step works
+on a freshly flushed L2 (a 256 MiB buffer is written between steps, outside
+the timed events); the per-step device times are summed.  Multi-GPU runs are
+independent replicas (each rank its own image; no collective on the data
+path), reported as weak scaling.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+ROWS = COLS = 4096
+N_SOURCES = 20000
+WORKLOAD = "fft2_butterworth_ifft2_4096x4096_fp32"
+METRIC = "2D FFT→filter→IFFT GB/s & % HBM peak at 4096² fp32, rel-L2 vs FP64 oracle"
+COMPULSORY_BYTES_PER_PX = 12  # img 4 + H 4 + out 4
+NOMINAL_C2C_BYTES_PER_PX = 44  # three-pass complex-to-complex schedule
+# algorithmic bytes per pixel of each stage of the half-spectrum schedule
+STAGE_BYTES_PER_PX = {"rows_fwd": 8, "cols_filter": 12, "rows_inv": 8}
+FLOPS_PER_IMAGE = 2 * 5 * ROWS * COLS * math.log2(ROWS * COLS) + 2 * ROWS * COLS
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_cs_0103001_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode())
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(stage: str):
+    """DRAM bytes per launch of `stage` from the committed ncu summary, if it
+    was taken on the current kernel sources (else None)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    src = kernel_source_hash()
+    with open(path) as f:
+        for line in f:
+            parts = line.split()
+            if len(parts) >= 3 and not line.startswith("#") and parts[0] == stage and parts[1] == src:
+                return float(parts[2])
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for line in self.lines:
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 7:
+                continue
+            try:
+                sm.append(float(p[0]))
+                smax.append(float(p[1]))
+            except ValueError:
+                continue
+            for name, v in zip(names, p[3:7]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_inputs(rank: int):
+    from paper_cs_0103001_gb300 import synth
+
+    img = synth.sky(ROWS, COLS, N_SOURCES, 3, rank)
+    H = synth.butterworth_lowpass(ROWS, COLS, 4, 0.1)
+    return img, H
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def run_gbfft(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_cs_0103001_gb300 as gb
+    from paper_cs_0103001_gb300 import _native as nat
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    img_np, H_np = make_inputs(rank)
+    img = torch.from_numpy(img_np).to(dev)
+    H = torch.from_numpy(H_np).to(dev)
+    out = torch.empty_like(img)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    plan = gb.Plan2D(ROWS, COLS, 1, dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        plan.filter(img, H, out=out)
+
+    # ---- device-time loop (inputs resident in HBM, L2 flushed between steps)
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize(dev)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    phys = vis.split(",")[local] if vis and len(vis.split(",")) > local else str(local)
+    clocks = ClockSampler(phys)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize(dev)
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    torch.cuda.synchronize(dev)
+    barrier()
+    wall = time.perf_counter() - wall0
+    clk = clocks.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms_local = sum(step_ms) / len(step_ms)
+    ms = ms_local
+    if world > 1:
+        t = torch.tensor([ms_local], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+
+    # ---- per-stage times (profile events around each launch) over K more steps
+    plan.set_option(nat.OPT_PROFILE, 1)
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)
+        step()
+    torch.cuda.synchronize(dev)
+    stages = plan.profile_read()
+    plan.set_option(nat.OPT_PROFILE, 0)
+    launches_per_step = sum(c for _, c in stages.values()) / args.steps
+
+    # ---- end to end through the public API: pinned host in, host out
+    img_h = torch.from_numpy(img_np).pin_memory()
+    H_h = torch.from_numpy(H_np).pin_memory()
+    out_h = torch.empty(ROWS, COLS, dtype=torch.float32).pin_memory()
+    img_d = torch.empty_like(img)
+    H_d = torch.empty_like(H)
+    e_steps = max(3, min(args.steps, 20))
+    for _ in range(2):
+        img_d.copy_(img_h, non_blocking=True)
+        H_d.copy_(H_h, non_blocking=True)
+        gb.fft2_filter_ifft2(img_d, H_d)
+    torch.cuda.synchronize(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(e_steps):
+        img_d.copy_(img_h, non_blocking=True)
+        H_d.copy_(H_h, non_blocking=True)
+        o = gb.fft2_filter_ifft2(img_d, H_d)
+        out_h.copy_(o, non_blocking=True)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = e0.elapsed_time(e1) / e_steps
+    if world > 1:
+        t = torch.tensor([e2e_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+
+    result = None
+    if rank == 0:
+        peak, peak_kind = measured_peaks()
+        px = ROWS * COLS
+        value = world * COMPULSORY_BYTES_PER_PX * px / (ms * 1e-3) / 1e9
+        # dominant kernel
+        dom = max(stages, key=lambda k: stages[k][0])
+        dom_ms = stages[dom][0] / stages[dom][1]
+        dom_bytes = STAGE_BYTES_PER_PX.get(dom, 0) * px
+        achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
+        traffic = recorded_traffic(dom)
+        # CPU baseline: the FP64 oracle on the same image, all host cores
+        import oracle
+
+        t0 = time.perf_counter()
+        ref = oracle.pipeline(img_np, H_np)
+        cpu_s = time.perf_counter() - t0
+        got = out.cpu().numpy().astype(np.float64)
+        rel = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
+        tol = 2e-7 * math.log2(px)
+        result = {
+            "metric": METRIC,
+            "value": round(value, 1),
+            "unit": "GB/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": round(ms, 5),
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "rows": ROWS, "cols": COLS, "images_per_step_per_gpu": 1,
+                       "sources": N_SOURCES, "filter": "butterworth order 4, cutoff 0.1 Nyquist",
+                       "l2": "flushed between steps (256 MiB write outside the timed events)",
+                       "parallelism": f"replicas x{world}"},
+            "pct_hbm_peak": round(100.0 * value / (world * peak), 2),
+            "us_per_image": round(ms * 1e3, 2),
+            "images_per_s": round(world * 1e3 / ms, 1),
+            "gflops_5nlogn": round(world * FLOPS_PER_IMAGE / (ms * 1e-3) / 1e9, 1),
+            "effective_gbs_c2c_44Bpx": round(world * NOMINAL_C2C_BYTES_PER_PX * px / (ms * 1e-3) / 1e9, 1),
+            "rel_l2": rel,
+            "rel_l2_tol": tol,
+            "rel_l2_pass": rel <= tol,
+            "stage_us": {k: round(1e3 * v[0] / v[1], 2) for k, v in stages.items()},
+            "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
+                         "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                         "traffic": traffic, "algorithmic_bytes": dom_bytes},
+            "cpu_baseline": {"value": round(COMPULSORY_BYTES_PER_PX * px / cpu_s / 1e9, 4), "unit": "GB/s",
+                             "cores": oracle.max_threads(), "kind": "oracle",
+                             "sample": "one 4096x4096 image through the FP64 C oracle pipeline",
+                             "seconds": round(cpu_s, 3)},
+            "e2e": {"value": round(world * COMPULSORY_BYTES_PER_PX * px / (e2e_ms * 1e-3) / 1e9, 1), "unit": "GB/s",
+                    "ms_per_step": round(e2e_ms, 4), "h2d_bytes_per_step": 2 * 4 * px,
+                    "d2h_bytes_per_step": 4 * px},
+            "gpu_launches": int(round(launches_per_step * args.steps)),
+            "clocks": clk,
+            "wall_s_timed": round(wall, 4),
+        }
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return result
+
+
+def run_reference(args):
+    """The FP64 C oracle as the reference arm, on the host cores."""
+    world, rank, _ = dist_setup()
+    if rank != 0:
+        return None
+    import oracle
+
+    img, H = make_inputs(0)
+    for _ in range(args.warmup):
+        oracle.pipeline(img, H)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.pipeline(img, H)
+    dt = (time.perf_counter() - t0) / args.steps
+    px = ROWS * COLS
+    value = COMPULSORY_BYTES_PER_PX * px / dt / 1e9
+    return {
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GB/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "rows": ROWS, "cols": COLS, "images_per_step_per_gpu": 1},
+        "cpu_baseline": {"value": round(value, 4), "unit": "GB/s", "cores": oracle.max_threads(), "kind": "oracle",
+                         "sample": "one 4096x4096 image per step through the FP64 C oracle pipeline"},
+        "e2e": {"value": round(value, 4), "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gbfft", choices=["gbfft", "reference"])
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "gbfft":
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        res = run_reference(args)
+    else:
+        import __graft_entry__
+
+        __graft_entry__._build_module().build()
+        res = run_gbfft(args)
+    if res is not None:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,174 @@
+/*
+ * gbfft.h — C ABI of the GB300 FFT -> filter -> IFFT library (libgbfft.so).
+ *
+ * The library computes the transforms of Higuera, Sarria, Fonseca and
+ * Idarraga, "Construction of an algorithm in parallel for the Fast Fourier
+ * Transform" (arXiv cs/0103001) with hand-written CUDA kernels for sm_103a:
+ *
+ *   forward (Eq. E2 / Eq. coefFourier):  c_k = (1/N) sum_j f_j exp(-2 pi i k j / N)
+ *   inverse (Eq. E3 at x_j = 2 pi j/N):  f_j = sum_k c_k exp(+2 pi i k j / N)   (no scale)
+ *   2D (Sec. 4): rows, then columns; the per-axis convention (1/M on rows,
+ *      1/N on columns) by default, Eq. 5 on request
+ *   application (Sec. 5): out = Re(ifft2(H . fft2(img))) for a real image and
+ *      a real filter H given in natural (unshifted) frequency order
+ *
+ * Conventions for every entry point:
+ *   - Each call returns an int status (gbfft_status); nothing throws or exits.
+ *   - Every data pointer is a DEVICE pointer owned by the caller, aligned to
+ *     16 bytes (else GBFFT_ERR_MISALIGNED).  The library allocates no device
+ *     memory: the caller provides a workspace sized by
+ *     fft_plan_workspace_bytes() and binds it with fft_plan_bind_workspace().
+ *   - Work is enqueued on the given stream and is asynchronous to the host.
+ *     A plan holds host state only; one plan must not be used from two
+ *     streams or threads at the same time.
+ *   - Complex data are interleaved (re, im): complex64 = 2 x float32,
+ *     complex128 = 2 x float64 (the paper ships each complex as a pair of
+ *     real columns, Sec. 2).
+ *   - Lengths are powers of two, N = 2^m with m >= 1 (Sec. 3); other lengths
+ *     return GBFFT_ERR_INVALID_SIZE.
+ *   - Launch failures are reported as GBFFT_ERR_CUDA; gbfft_last_cuda_error()
+ *     gives the CUDA error code.
+ */
+#ifndef GBFFT_H
+#define GBFFT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* A CUDA stream (layout-compatible with cudaStream_t); NULL = legacy stream. */
+typedef struct CUstream_st *gbfft_stream_t;
+
+typedef struct gbfft_plan *gbfft_plan_t;
+
+typedef enum {
+    GBFFT_C64 = 1,  /* complex64: float32 pairs; 2D images are float32 */
+    GBFFT_C128 = 2, /* complex128: float64 pairs; 2D images are float64 */
+} gbfft_dtype;
+
+typedef enum {
+    GBFFT_OK = 0,
+    GBFFT_ERR_NULL = -1,         /* a required pointer is NULL */
+    GBFFT_ERR_INVALID_SIZE = -2, /* length not 2^m, m out of range, batch < 1 */
+    GBFFT_ERR_DTYPE = -3,        /* unknown or unsupported dtype for this call */
+    GBFFT_ERR_MISALIGNED = -4,   /* a data pointer is not 16-byte aligned */
+    GBFFT_ERR_WORKSPACE = -5,    /* no workspace bound, or the one given is too small */
+    GBFFT_ERR_UNSUPPORTED = -6,  /* valid request this build does not implement */
+    GBFFT_ERR_CUDA = -7,         /* a CUDA call or kernel launch failed */
+    GBFFT_ERR_TIMEOUT = -8,      /* a bounded device-side wait gave up */
+    GBFFT_ERR_INVALID_VALUE = -9 /* bad option key/value or wrong plan kind */
+} gbfft_status;
+
+/* Plan options (fft_plan_set_option). */
+typedef enum {
+    /* 2D scale convention: 0 = per-axis (default; forward 1/(N M), inverse 1),
+     * 1 = Eq. 5 (forward 1/N with N = rows, inverse 1/M).  The filtered image
+     * of fft2_filter_ifft2 is the same under both. */
+    GBFFT_OPT_SCALE_CONVENTION = 1,
+    /* Element stride between the filters of consecutive images in a batch:
+     * 0 (default) shares one H; rows*cols gives each image its own. */
+    GBFFT_OPT_H_BATCH_STRIDE = 2,
+    /* Arithmetic of the butterflies: 0 = FP32 (default for C64),
+     * 1 = split-BF16 tensor-core radix-16 stages (C64 only). */
+    GBFFT_OPT_PRECISION = 3,
+    /* 2D: number of images whose spectra share the workspace at a time
+     * (0 = choose from the L2 size).  Changes fft_plan_workspace_bytes. */
+    GBFFT_OPT_IMAGES_PER_CHUNK = 4,
+    /* 1 = record a CUDA event pair around every kernel launch of this plan
+     * (read with gbfft_plan_profile_read); 0 (default) = off. */
+    GBFFT_OPT_PROFILE = 5
+} gbfft_option;
+
+/* Stages reported by gbfft_plan_profile_read. */
+typedef enum {
+    GBFFT_STAGE_FFT1D = 0,     /* one-pass batched 1D transform */
+    GBFFT_STAGE_FOURSTEP_A = 1,/* four-step pass A (column FFTs + twiddle) */
+    GBFFT_STAGE_FOURSTEP_B = 2,/* four-step pass B (row FFTs, transposed store) */
+    GBFFT_STAGE_ROWS_FWD = 3,  /* 2D row pass, forward (real rows -> half spectra) */
+    GBFFT_STAGE_COLS = 4,      /* 2D fused column pass: FFT -> x s H -> IFFT */
+    GBFFT_STAGE_ROWS_INV = 5,  /* 2D row pass, inverse (half spectra -> real rows) */
+    GBFFT_STAGE_COLS_GRAD = 6, /* 2D fused column pass of the adjoint (grad_H) */
+    GBFFT_STAGE_TWIDDLES = 7,  /* twiddle-table generation (bind time) */
+    GBFFT_STAGE_COUNT = 8
+} gbfft_stage;
+
+/* ---- plans --------------------------------------------------------------- */
+
+/* 1D batched complex-to-complex plan: `batch` contiguous transforms of length
+ * n = 2^m, 1 <= m <= 24 (Eq. E2 forward, Eq. E3 inverse).  dtype C64 or C128.
+ * On success *out receives a new plan (free with fft_plan_destroy). */
+int fft_plan_create(int64_t n, int64_t batch, int dtype, gbfft_plan_t *out);
+
+/* 2D plan for the Sec. 5 pipeline on `batch` real images of rows x cols
+ * (row-major, rows = N = 2^a, cols = M = 2^b, 2 <= N, M <= 8192).
+ * dtype C64 (float32 images). */
+int fft2_plan_create(int64_t rows, int64_t cols, int64_t batch, int dtype, gbfft_plan_t *out);
+
+/* Set a gbfft_option.  Returns GBFFT_ERR_INVALID_VALUE for an unknown key or
+ * an out-of-range value.  Options that change the workspace size must be set
+ * before fft_plan_bind_workspace. */
+int fft_plan_set_option(gbfft_plan_t plan, int key, int64_t value);
+
+/* Bytes of device workspace the plan needs (twiddle tables + spectra). */
+int fft_plan_workspace_bytes(gbfft_plan_t plan, size_t *bytes);
+
+/* Bind caller-owned device memory (>= fft_plan_workspace_bytes, 256-byte
+ * aligned) as the plan's workspace and enqueue the generation of its twiddle
+ * tables on `stream` (FP64 arithmetic, each factor rounded once).  The memory
+ * must stay valid until the plan is destroyed or re-bound. */
+int fft_plan_bind_workspace(gbfft_plan_t plan, void *workspace, size_t bytes, gbfft_stream_t stream);
+
+/* 1D forward transform of a 1D plan: out = (1/N) DFT(in) per transform
+ * (Eq. E2).  in and out hold batch x n complex values of the plan's dtype;
+ * in == out (in place) is allowed, partial overlap is not. */
+int fft_forward(gbfft_plan_t plan, const void *in, void *out, gbfft_stream_t stream);
+
+/* 1D inverse transform: out_j = sum_k in_k exp(+2 pi i j k / N), unscaled
+ * (Eq. E3).  Same layout and aliasing rules as fft_forward. */
+int fft_inverse(gbfft_plan_t plan, const void *in, void *out, gbfft_stream_t stream);
+
+/* Sec. 5 pipeline on a 2D plan: for each image b,
+ *   out_b = Re(ifft2(H_b . fft2(img_b)))
+ * img, out: batch x rows x cols float32 (row-major).  H: rows x cols float32
+ * real filter in natural (unshifted) DFT order; image b uses
+ * H + b * h_batch_stride (option GBFFT_OPT_H_BATCH_STRIDE, default 0).
+ * The filter multiplies the real and the imaginary part of every spectral
+ * value.  img == out is allowed. */
+int fft2_filter_ifft2(gbfft_plan_t plan, const float *img, const float *H, float *out, gbfft_stream_t stream);
+
+/* Adjoint of fft2_filter_ifft2 for an upstream gradient grad_out = dL/dout:
+ *   grad_img_b = Re(ifft2(H . fft2(grad_out_b)))          (same shape as img)
+ *   grad_H[k]  = N M sum_b Re(conj(fft2(grad_out_b)[k]) fft2(img_b)[k])
+ * with per-axis spectra; H is shared (h_batch_stride must be 0) and grad_H
+ * (rows x cols float32) is overwritten with the sum over the batch.
+ * grad_img may be NULL (then only grad_H is produced) and so may grad_H. */
+int fft2_filter_ifft2_backward(gbfft_plan_t plan, const float *img, const float *H, const float *grad_out,
+                               float *grad_img, float *grad_H, gbfft_stream_t stream);
+
+/* Destroy a plan (host state only; the workspace belongs to the caller). */
+int fft_plan_destroy(gbfft_plan_t plan);
+
+/* ---- diagnostics ---------------------------------------------------------- */
+
+/* Static string for a status code. */
+const char *gbfft_status_string(int status);
+
+/* The cudaError_t code behind the last GBFFT_ERR_CUDA on this host thread. */
+int gbfft_last_cuda_error(void);
+
+/* With GBFFT_OPT_PROFILE on: wait for the recorded events, add the elapsed
+ * milliseconds and launch counts per gbfft_stage into ms[0..nstages) and
+ * launches[0..nstages) (either may be NULL), then forget the records. */
+int gbfft_plan_profile_read(gbfft_plan_t plan, double *ms, int64_t *launches, int nstages);
+
+/* Library version as 10000*major + 100*minor + patch. */
+int gbfft_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GBFFT_H */

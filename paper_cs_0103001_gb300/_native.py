@@ -1,0 +1,95 @@
+"""ctypes binding of libgbfft.so (the C ABI in include/gbfft.h).
+
+Argument marshalling only: every transform runs in the library's CUDA
+kernels.  There is no fallback: if the library is missing or fails to load,
+importing this module raises.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libgbfft.so")
+
+# gbfft_dtype
+C64 = 1
+C128 = 2
+
+# gbfft_status
+OK = 0
+ERR_NULL = -1
+ERR_INVALID_SIZE = -2
+ERR_DTYPE = -3
+ERR_MISALIGNED = -4
+ERR_WORKSPACE = -5
+ERR_UNSUPPORTED = -6
+ERR_CUDA = -7
+ERR_TIMEOUT = -8
+ERR_INVALID_VALUE = -9
+
+# gbfft_option
+OPT_SCALE_CONVENTION = 1
+OPT_H_BATCH_STRIDE = 2
+OPT_PRECISION = 3
+OPT_IMAGES_PER_CHUNK = 4
+OPT_PROFILE = 5
+
+# gbfft_stage
+STAGES = ("fft1d", "fourstep_a", "fourstep_b", "rows_fwd", "cols_filter", "rows_inv", "cols_grad", "twiddles")
+
+# every exported symbol with (restype, argtypes)
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_INT = ctypes.c_int
+SIGNATURES = {
+    "fft_plan_create": (_INT, [_I64, _I64, _INT, ctypes.POINTER(_P)]),
+    "fft2_plan_create": (_INT, [_I64, _I64, _I64, _INT, ctypes.POINTER(_P)]),
+    "fft_plan_set_option": (_INT, [_P, _INT, _I64]),
+    "fft_plan_workspace_bytes": (_INT, [_P, ctypes.POINTER(ctypes.c_size_t)]),
+    "fft_plan_bind_workspace": (_INT, [_P, _P, ctypes.c_size_t, _P]),
+    "fft_forward": (_INT, [_P, _P, _P, _P]),
+    "fft_inverse": (_INT, [_P, _P, _P, _P]),
+    "fft2_filter_ifft2": (_INT, [_P, _P, _P, _P, _P]),
+    "fft2_filter_ifft2_backward": (_INT, [_P, _P, _P, _P, _P, _P, _P]),
+    "fft_plan_destroy": (_INT, [_P]),
+    "gbfft_status_string": (ctypes.c_char_p, [_INT]),
+    "gbfft_last_cuda_error": (_INT, []),
+    "gbfft_plan_profile_read": (_INT, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64), _INT]),
+    "gbfft_version": (_INT, []),
+}
+
+
+class GbfftError(RuntimeError):
+    def __init__(self, fn: str, status: int):
+        self.status = status
+        msg = lib.gbfft_status_string(status).decode() if lib is not None else str(status)
+        extra = f" (cudaError {lib.gbfft_last_cuda_error()})" if status == ERR_CUDA else ""
+        super().__init__(f"{fn} failed: {msg} [{status}]{extra}")
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(
+            f"libgbfft.so not found at {LIB_PATH}: build it first "
+            "(python -c 'import __graft_entry__ as g; g.build()')"
+        )
+    so = ctypes.CDLL(LIB_PATH)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(so, name)
+        fn.restype = res
+        fn.argtypes = args
+    return so
+
+
+lib = _load()
+
+
+def check(fn: str, status: int) -> None:
+    if status != OK:
+        raise GbfftError(fn, status)
+
+
+def call(fn: str, *args) -> None:
+    check(fn, getattr(lib, fn)(*args))

@@ -1,0 +1,222 @@
+"""PyTorch front end of the gbfft library.
+
+PyTorch supplies device memory (the caching allocator) and streams; every
+transform runs in libgbfft.so's CUDA kernels, reached through the C ABI with
+raw device pointers.  Functions here:
+
+  fft(x), ifft(x)           1D transforms over the last axis (Eq. E2 / Eq. E3)
+  fft2_filter_ifft2(img, H) the Sec. 5 pipeline, differentiable in img and H
+  Plan1D, Plan2D            explicit plans (workspace owned by a torch tensor)
+"""
+
+from __future__ import annotations
+
+import ctypes
+import threading
+
+import torch
+
+from . import _native as nat
+
+_P = ctypes.c_void_p
+
+
+def _stream_handle(device: torch.device) -> _P:
+    return _P(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _ptr(t: torch.Tensor) -> _P:
+    return _P(t.data_ptr())
+
+
+def _require_cuda(t: torch.Tensor, what: str) -> None:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError(f"{what} must be a CUDA tensor (gbfft has no CPU path)")
+
+
+class _PlanBase:
+    """Owns a gbfft plan handle and its workspace tensor."""
+
+    def __init__(self, handle: _P, device: torch.device, options: dict[int, int] | None):
+        self.handle = handle
+        self.device = device
+        for key, value in (options or {}).items():
+            nat.call("fft_plan_set_option", self.handle, int(key), int(value))
+        nbytes = ctypes.c_size_t(0)
+        nat.call("fft_plan_workspace_bytes", self.handle, ctypes.byref(nbytes))
+        self.workspace_bytes = int(nbytes.value)
+        with torch.cuda.device(device):
+            # 256-byte aligned by the caching allocator
+            self.workspace = torch.empty(max(self.workspace_bytes, 256), dtype=torch.uint8, device=device)
+            nat.call("fft_plan_bind_workspace", self.handle, _ptr(self.workspace), self.workspace.numel(),
+                     _stream_handle(device))
+            # twiddle tables must be complete before another stream uses the plan
+            torch.cuda.current_stream(device).synchronize()
+        self.lock = threading.Lock()
+
+    def set_option(self, key: int, value: int) -> None:
+        nat.call("fft_plan_set_option", self.handle, int(key), int(value))
+
+    def profile_read(self) -> dict[str, tuple[float, int]]:
+        n = len(nat.STAGES)
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_int64 * n)()
+        nat.call("gbfft_plan_profile_read", self.handle, ms, cnt, n)
+        return {name: (ms[i], cnt[i]) for i, name in enumerate(nat.STAGES) if cnt[i]}
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and nat.lib is not None:
+            nat.lib.fft_plan_destroy(h)
+            self.handle = None
+
+
+class Plan1D(_PlanBase):
+    """Batched 1D C2C plan: `batch` contiguous transforms of length n = 2^m."""
+
+    def __init__(self, n: int, batch: int, dtype: torch.dtype, device, options=None):
+        code = {torch.complex64: nat.C64, torch.complex128: nat.C128}.get(dtype)
+        if code is None:
+            raise TypeError(f"unsupported dtype {dtype}; use complex64 or complex128")
+        h = _P()
+        nat.call("fft_plan_create", int(n), int(batch), code, ctypes.byref(h))
+        self.n, self.batch, self.dtype = int(n), int(batch), dtype
+        super().__init__(h, torch.device(device), options)
+
+    def forward(self, x: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        return self._run("fft_forward", x, out)
+
+    def inverse(self, x: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        return self._run("fft_inverse", x, out)
+
+    def _run(self, fn: str, x: torch.Tensor, out: torch.Tensor | None) -> torch.Tensor:
+        if x.dtype != self.dtype or x.numel() != self.n * self.batch or not x.is_contiguous():
+            raise ValueError("input does not match the plan (dtype, size, contiguity)")
+        if out is None:
+            out = torch.empty_like(x)
+        with self.lock:
+            nat.call(fn, self.handle, _ptr(x), _ptr(out), _stream_handle(x.device))
+        return out
+
+
+class Plan2D(_PlanBase):
+    """Sec. 5 pipeline plan for `batch` float32 images of rows x cols."""
+
+    def __init__(self, rows: int, cols: int, batch: int, device, options=None):
+        h = _P()
+        nat.call("fft2_plan_create", int(rows), int(cols), int(batch), nat.C64, ctypes.byref(h))
+        self.rows, self.cols, self.batch = int(rows), int(cols), int(batch)
+        self.h_stride = int((options or {}).get(nat.OPT_H_BATCH_STRIDE, 0))
+        super().__init__(h, torch.device(device), options)
+
+    def filter(self, img: torch.Tensor, H: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty_like(img)
+        with self.lock:
+            nat.call("fft2_filter_ifft2", self.handle, _ptr(img), _ptr(H), _ptr(out), _stream_handle(img.device))
+        return out
+
+    def backward(self, img, H, grad_out, grad_img=None, grad_H=None):
+        with self.lock:
+            nat.call("fft2_filter_ifft2_backward", self.handle, _ptr(img), _ptr(H), _ptr(grad_out),
+                     _ptr(grad_img) if grad_img is not None else _P(),
+                     _ptr(grad_H) if grad_H is not None else _P(), _stream_handle(img.device))
+        return grad_img, grad_H
+
+
+_cache: dict[tuple, _PlanBase] = {}
+_cache_lock = threading.Lock()
+
+
+def _cached(key, make):
+    with _cache_lock:
+        p = _cache.get(key)
+        if p is None:
+            p = make()
+            _cache[key] = p
+        return p
+
+
+def clear_plan_cache() -> None:
+    with _cache_lock:
+        _cache.clear()
+
+
+def _plan1d(x: torch.Tensor) -> Plan1D:
+    n = x.shape[-1]
+    batch = x.numel() // n
+    key = ("1d", n, batch, x.dtype, x.device)
+    return _cached(key, lambda: Plan1D(n, batch, x.dtype, x.device))
+
+
+def fft(x: torch.Tensor) -> torch.Tensor:
+    """c = (1/N) sum_j x_j exp(-2 pi i jk/N) over the last axis (Eq. E2)."""
+    _require_cuda(x, "x")
+    x = x.contiguous()
+    return _plan1d(x).forward(x)
+
+
+def ifft(c: torch.Tensor) -> torch.Tensor:
+    """f = sum_k c_k exp(+2 pi i jk/N) over the last axis, unscaled (Eq. E3)."""
+    _require_cuda(c, "c")
+    c = c.contiguous()
+    return _plan1d(c).inverse(c)
+
+
+def _plan2d(img: torch.Tensor, per_image_H: bool) -> Plan2D:
+    rows, cols = img.shape[-2:]
+    batch = img.numel() // (rows * cols)
+    opts = {nat.OPT_H_BATCH_STRIDE: rows * cols if per_image_H else 0}
+    key = ("2d", rows, cols, batch, per_image_H, img.device)
+    return _cached(key, lambda: Plan2D(rows, cols, batch, img.device, opts))
+
+
+def _check_2d(img: torch.Tensor, H: torch.Tensor) -> bool:
+    _require_cuda(img, "img")
+    _require_cuda(H, "H")
+    if img.dtype != torch.float32 or H.dtype != torch.float32:
+        raise TypeError("img and H must be float32")
+    if img.dim() < 2:
+        raise ValueError("img must be [..., rows, cols]")
+    if H.shape == img.shape[-2:]:
+        return False
+    if H.shape == img.shape:
+        return True
+    raise ValueError(f"H shape {tuple(H.shape)} must be {tuple(img.shape[-2:])} or {tuple(img.shape)}")
+
+
+class _FilterFn(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, img, H):
+        per_image = _check_2d(img, H)
+        img_c, H_c = img.contiguous(), H.contiguous()
+        out = _plan2d(img_c, per_image).filter(img_c, H_c)
+        ctx.save_for_backward(img_c, H_c)
+        ctx.per_image = per_image
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        img, H = ctx.saved_tensors
+        g = grad_out.contiguous()
+        plan = _plan2d(img, ctx.per_image)
+        need_img, need_H = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+        if ctx.per_image:
+            if need_H:
+                raise NotImplementedError("grad of a per-image filter stack is not supported; share one H")
+            # the adjoint of the pipeline is the pipeline itself (real H)
+            return plan.filter(g, H), None
+        grad_img = torch.empty_like(img) if need_img else None
+        grad_H = torch.empty_like(H) if need_H else None
+        plan.backward(img, H, g, grad_img, grad_H)
+        return grad_img, grad_H
+
+
+def fft2_filter_ifft2(img: torch.Tensor, H: torch.Tensor) -> torch.Tensor:
+    """Sec. 5: Re(ifft2(H * fft2(img))) for float32 images [..., rows, cols].
+
+    H is a real float32 filter [rows, cols] (shared) or one per image (same
+    shape as img), in natural (unshifted) DFT order.  Differentiable in img
+    and (for a shared H) in H.
+    """
+    return _FilterFn.apply(img, H)

@@ -1,0 +1,179 @@
+// fourstep.cu — batched 1D transforms longer than one thread block can hold.
+//
+// The paper splits the radix-2 tree of a length-N transform between 2^l
+// processes (Sec. 2): each owns a subtree up to level m1 = m - l, and the
+// upper levels combine the partial transforms.  On one GPU the same split is
+// made along index bits, N = N1 * N2 (the "four-step" factorisation):
+//   j = j1 N2 + j2,  k = k1 + N1 k2,
+//   X[k1 + N1 k2] = sum_j2 W_N2^(j2 k2) [ W_N^(j2 k1) sum_j1 x[j1 N2 + j2] W_N1^(j1 k1) ].
+// Pass A runs the inner length-N1 transforms down the columns j2 of the
+// N1 x N2 row-major view and multiplies by W_N^(j2 k1) (two-level table);
+// pass B runs the outer length-N2 transforms along the rows k1 and stores
+// bin k2 of row k1 at k1 + N1 k2, the natural order of X.  Both passes move a
+// tile of W adjacent columns (pass A) or rows (pass B) per thread block so
+// every global access is a run of W or 32/W contiguous elements.  The
+// intermediate goes to a workspace chunk sized to stay in L2 when it can.
+#include "fft_core.cuh"
+#include "internal.h"
+
+namespace gbfft {
+
+template <int N, typename R> struct FsCfg {
+    static constexpr int E = N < 16 ? N : 16;
+    static constexpr int T = N / E;
+    static constexpr int SMEM_ELEMS = (sizeof(R) == 4 ? 16384 : 8192);
+    static constexpr int W0 = SMEM_ELEMS / N < 512 / T ? SMEM_ELEMS / N : 512 / T;
+    static constexpr int WMAX = W0 > 64 ? 64 : (W0 < 1 ? 1 : W0);
+};
+
+int fourstep_split(int log2n, bool dbl, int *log2n1, int *log2n2) {
+    (void)dbl;
+    *log2n1 = log2n / 2;
+    *log2n2 = log2n - log2n / 2;
+    return 0;
+}
+
+// W_N^idx (forward sign) from the two-level table: fine W_N^b, b < F; coarse W_N^(aF).
+template <typename C>
+__device__ __forceinline__ C tw_two_level(const C *__restrict__ t4, int idx, int log2f) {
+    const int f = 1 << log2f;
+    const C lo = __ldg(t4 + (idx & (f - 1)));
+    const C hi = __ldg(t4 + f + (idx >> log2f));
+    return cmul(hi, lo);
+}
+
+// Pass A: column transforms of length N1 (= N) over the N1 x n2 view.
+template <int N, int DIR, typename R>
+__global__ void __launch_bounds__(512)
+    k_fourstep_a(const typename cvec<R>::type *in, typename cvec<R>::type *tmp, int log2n2,
+                 const typename cvec<R>::type *__restrict__ tw, const typename cvec<R>::type *__restrict__ t4,
+                 int log2f) {
+    typedef typename cvec<R>::type C;
+    typedef FsCfg<N, R> K;
+    constexpr int E = K::E, T = K::T, W = K::WMAX;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C *sm = reinterpret_cast<C *>(smraw);
+    const int w = threadIdx.x % W;
+    const int t = threadIdx.x / W;
+    const int j2 = blockIdx.x * W + w;
+    const size_t base = (size_t)blockIdx.y * ((size_t)N << log2n2) + j2;
+    C v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = in[base + ((size_t)(t + T * e) << log2n2)];
+    fft_regs<N, E, DIR>(v, sm + w, tw, t, W);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int k1 = t + T * e;
+        const C f = tw_two_level(t4, k1 * j2, log2f);  // k1 j2 < N1 n2: no reduction needed
+        v[e] = DIR < 0 ? cmul(v[e], f) : cmulc(v[e], f);
+        tmp[base + ((size_t)k1 << log2n2)] = v[e];
+    }
+}
+
+// Pass B: row transforms of length N2 (= N) over the n1 x N2 view, stored at k1 + n1 k2.
+template <int N, int DIR, typename R>
+__global__ void __launch_bounds__(512)
+    k_fourstep_b(const typename cvec<R>::type *tmp, typename cvec<R>::type *out, int log2n1,
+                 const typename cvec<R>::type *__restrict__ tw, R scale) {
+    typedef typename cvec<R>::type C;
+    typedef FsCfg<N, R> K;
+    constexpr int E = K::E, T = K::T, W = K::WMAX;
+    extern __shared__ __align__(16) unsigned char smraw[];
+    C *sm = reinterpret_cast<C *>(smraw);
+    const int w = threadIdx.x % W;
+    const int t = threadIdx.x / W;
+    const int k1 = blockIdx.x * W + w;
+    const size_t img = (size_t)blockIdx.y * ((size_t)N << log2n1);
+    const C *row = tmp + img + (size_t)k1 * N;
+    C v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = row[t + T * e];
+    fft_regs<N, E, DIR>(v, sm + w, tw, t, W);
+    C *dst = out + img + k1;
+#pragma unroll
+    for (int e = 0; e < E; ++e) dst[(size_t)(t + T * e) << log2n1] = cscale(v[e], scale);
+}
+
+template <int N, typename R>
+static cudaError_t run_a(const void *in, void *tmp, int log2n2, long long nb, int dir, const void *tw,
+                         const void *t4, int log2f, cudaStream_t s) {
+    typedef typename cvec<R>::type C;
+    typedef FsCfg<N, R> K;
+    constexpr int W = K::WMAX;  // <= 64 <= the other factor (>= 2^7)
+    const size_t smem = (size_t)padded_len(N) * W * sizeof(C);
+    auto kern = dir < 0 ? k_fourstep_a<N, -1, R> : k_fourstep_a<N, 1, R>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    if (nb > 65535) return cudaErrorInvalidConfiguration;
+    dim3 grid((1 << log2n2) / W, (unsigned)nb);
+    kern<<<grid, W * K::T, smem, s>>>(static_cast<const C *>(in), static_cast<C *>(tmp), log2n2,
+                                      static_cast<const C *>(tw), static_cast<const C *>(t4), log2f);
+    return cudaGetLastError();
+}
+
+template <int N, typename R>
+static cudaError_t run_b(const void *tmp, void *out, int log2n1, long long nb, int dir, const void *tw, double scale,
+                         cudaStream_t s) {
+    typedef typename cvec<R>::type C;
+    typedef FsCfg<N, R> K;
+    constexpr int W = K::WMAX;  // <= 64 <= the other factor (>= 2^7)
+    const size_t smem = (size_t)padded_len(N) * W * sizeof(C);
+    auto kern = dir < 0 ? k_fourstep_b<N, -1, R> : k_fourstep_b<N, 1, R>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    if (nb > 65535) return cudaErrorInvalidConfiguration;
+    dim3 grid((1 << log2n1) / W, (unsigned)nb);
+    kern<<<grid, W * K::T, smem, s>>>(static_cast<const C *>(tmp), static_cast<C *>(out), log2n1,
+                                      static_cast<const C *>(tw), (R)scale);
+    return cudaGetLastError();
+}
+
+// Factor lengths that occur for 2^14 <= N <= 2^24: 2^7 .. 2^12.
+#define GBFFT_FS_CASES(X) X(7) X(8) X(9) X(10) X(11) X(12)
+
+template <typename R>
+static cudaError_t dispatch_a(const void *in, void *tmp, int l1, int l2, long long nb, int dir, const void *tw,
+                              const void *t4, int log2f, cudaStream_t s) {
+    switch (l1) {
+#define GBFFT_A(L) \
+    case L: return run_a<(1 << L), R>(in, tmp, l2, nb, dir, tw, t4, log2f, s);
+        GBFFT_FS_CASES(GBFFT_A)
+#undef GBFFT_A
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename R>
+static cudaError_t dispatch_b(const void *tmp, void *out, int l1, int l2, long long nb, int dir, const void *tw,
+                              double scale, cudaStream_t s) {
+    switch (l2) {
+#define GBFFT_B(L) \
+    case L: return run_b<(1 << L), R>(tmp, out, l1, nb, dir, tw, scale, s);
+        GBFFT_FS_CASES(GBFFT_B)
+#undef GBFFT_B
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_fourstep_a(const void *in, void *tmp, int log2n, long long batch, bool dbl, int dir,
+                              const void *tw_n1, const void *tw_4s, cudaStream_t s) {
+    int l1, l2;
+    fourstep_split(log2n, dbl, &l1, &l2);
+    const int log2f = (log2n + 1) / 2;
+    return dbl ? dispatch_a<double>(in, tmp, l1, l2, batch, dir, tw_n1, tw_4s, log2f, s)
+               : dispatch_a<float>(in, tmp, l1, l2, batch, dir, tw_n1, tw_4s, log2f, s);
+}
+
+cudaError_t launch_fourstep_b(const void *tmp, void *out, int log2n, long long batch, bool dbl, int dir,
+                              const void *tw_n2, double scale, cudaStream_t s) {
+    int l1, l2;
+    fourstep_split(log2n, dbl, &l1, &l2);
+    return dbl ? dispatch_b<double>(tmp, out, l1, l2, batch, dir, tw_n2, scale, s)
+               : dispatch_b<float>(tmp, out, l1, l2, batch, dir, tw_n2, scale, s);
+}
+
+}  // namespace gbfft

@@ -1,0 +1,70 @@
+// twiddle.cu — per-plan twiddle tables, computed on the GPU in FP64.
+//
+// Table 2 of arXiv cs/0103001 keeps the vector Z_j = exp(-2 pi i j / N) of
+// all twiddle factors.  Each factor here is likewise computed from its exact
+// integer phase with the FP64 sincospi routine and rounded once to the
+// working precision; only the layout differs (per Stockham pass, see
+// fft_core.cuh, and a two-level table for the four-step inter-pass factors).
+#include "fft_core.cuh"
+#include "internal.h"
+
+namespace gbfft {
+
+template <typename C>
+__global__ void k_stockham_twiddles(C *tw, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int np = plan_passes(n);
+    if (np < 2 || i >= n - 1) return;
+    // pass p >= 1 owns entries [Ns_p - 1, Ns_{p+1} - 1), Ns_np = n
+    int p = 1;
+    while (p + 1 < np && i >= plan_stride(n, p + 1) - 1) ++p;
+    const int ns = plan_stride(n, p);
+    const int local = i - (ns - 1);
+    const int r = local / ns + 1;
+    const int m = local % ns;
+    const long long ph = (long long)r * m;          // exact phase numerator
+    const long long den = (long long)ns * plan_radix(n, p);
+    double s, c;
+    sincospi(-2.0 * (double)ph / (double)den, &s, &c);
+    tw[i] = C{(decltype(tw[0].x))c, (decltype(tw[0].x))s};
+}
+
+// Two-level table for W_n^idx, idx < n: entries [0, F) hold W_n^b (b < F),
+// entries [F, F + n/F) hold W_n^(a F) (a < n/F), with F = 2^ceil(log2(n)/2).
+template <typename C>
+__global__ void k_fourstep_twiddles(C *tw, int n, int log2f) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int f = 1 << log2f;
+    const int total = f + (n >> log2f);
+    if (i >= total) return;
+    const long long ph = i < f ? (long long)i : (long long)(i - f) << log2f;
+    double s, c;
+    sincospi(-2.0 * (double)ph / (double)n, &s, &c);
+    tw[i] = C{(decltype(tw[0].x))c, (decltype(tw[0].x))s};
+}
+
+cudaError_t launch_twiddles(void *tw, int n, bool dbl, cudaStream_t s) {
+    if (n < 2) return cudaSuccess;
+    const int threads = 256;
+    const int blocks = (n + threads - 1) / threads;
+    if (dbl)
+        k_stockham_twiddles<double2><<<blocks, threads, 0, s>>>(static_cast<double2 *>(tw), n);
+    else
+        k_stockham_twiddles<float2><<<blocks, threads, 0, s>>>(static_cast<float2 *>(tw), n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fourstep_twiddles(void *tw, int n, bool dbl, cudaStream_t s) {
+    const int L = ilog2(n);
+    const int log2f = (L + 1) / 2;
+    const int total = (1 << log2f) + (n >> log2f);
+    const int threads = 256;
+    const int blocks = (total + threads - 1) / threads;
+    if (dbl)
+        k_fourstep_twiddles<double2><<<blocks, threads, 0, s>>>(static_cast<double2 *>(tw), n, log2f);
+    else
+        k_fourstep_twiddles<float2><<<blocks, threads, 0, s>>>(static_cast<float2 *>(tw), n, log2f);
+    return cudaGetLastError();
+}
+
+}  // namespace gbfft

@@ -1,0 +1,137 @@
+"""GPU parity of the batched 1D transforms (Eq. E2 forward, Eq. E3 inverse)
+against the FP64 oracle, through the C ABI (via the ctypes binding)."""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_cs_0103001_gb300 import synth
+from tests.gpu_util import FP64_TOL, max_rel_l2, tol_fp32
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import torch
+
+    import paper_cs_0103001_gb300 as gb
+
+    assert torch.cuda.is_available()
+    return gb
+
+
+def _run(gb, x, inverse=False, dtype=None):
+    import torch
+
+    t = torch.from_numpy(x).cuda()
+    if dtype is not None:
+        t = t.to(dtype)
+    y = gb.ifft(t) if inverse else gb.fft(t)
+    return y.cpu().numpy()
+
+
+def _tol(n, dbl):
+    return FP64_TOL if dbl else tol_fp32(n)
+
+
+@pytest.mark.parametrize("dbl", [False, True], ids=["c64", "c128"])
+@pytest.mark.parametrize("log2n", range(1, 15))
+@pytest.mark.parametrize("batch", [1, 3, 17])
+def test_one_pass_all_sizes(gb, log2n, batch, dbl):
+    import torch
+
+    if dbl and log2n > 13:
+        pytest.skip("complex128 one-pass limit is 2^13 (four-step beyond)")
+    n = 1 << log2n
+    x = synth.complex_uniform((batch, n), 2, log2n, batch)
+    dt = torch.complex128 if dbl else None
+    xo = x.astype(np.complex128)
+    got = _run(gb, x, dtype=dt)
+    assert max_rel_l2(got, oracle.fft(xo), axes=-1) <= _tol(n, dbl)
+    got = _run(gb, x, inverse=True, dtype=dt)
+    assert max_rel_l2(got, oracle.ifft(xo), axes=-1) <= _tol(n, dbl)
+
+
+@pytest.mark.parametrize("dbl,log2n,batch", [
+    (False, 15, 3), (False, 16, 2), (False, 17, 3), (False, 18, 1), (False, 20, 2), (False, 22, 1),
+    (True, 14, 3), (True, 15, 2), (True, 17, 1), (True, 19, 2),
+])
+def test_four_step(gb, dbl, log2n, batch):
+    import torch
+
+    n = 1 << log2n
+    x = synth.complex_uniform((batch, n), 2, log2n, batch)
+    dt = torch.complex128 if dbl else None
+    xo = x.astype(np.complex128)
+    assert max_rel_l2(_run(gb, x, dtype=dt), oracle.fft(xo), axes=-1) <= _tol(n, dbl)
+    assert max_rel_l2(_run(gb, x, inverse=True, dtype=dt), oracle.ifft(xo), axes=-1) <= _tol(n, dbl)
+
+
+def test_in_place_and_plan_reuse(gb):
+    import torch
+
+    for n, batch in ((4096, 5), (1 << 16, 3)):
+        x = synth.complex_uniform((batch, n), 3, n)
+        plan = gb.Plan1D(n, batch, torch.complex64, "cuda")
+        t = torch.from_numpy(x).cuda()
+        plan.forward(t, out=t)  # in place
+        ref = oracle.fft(x.astype(np.complex128))
+        assert max_rel_l2(t.cpu().numpy(), ref, axes=-1) <= tol_fp32(n)
+        plan.inverse(t, out=t)
+        assert max_rel_l2(t.cpu().numpy(), oracle.ifft(ref), axes=-1) <= tol_fp32(n)
+        # a second call on the same plan gives the same bits
+        a = plan.forward(torch.from_numpy(x).cuda())
+        b = plan.forward(torch.from_numpy(x).cuda())
+        assert torch.equal(a, b)
+
+
+def test_closed_forms_on_gpu(gb):
+    """delta -> 1/N everywhere; a pure exponential -> one bin."""
+    n = 4096
+    d = np.zeros((1, n), np.complex64)
+    d[0, 0] = 1
+    got = _run(gb, d)
+    assert np.max(np.abs(got - 1.0 / n)) <= 1e-7 / n * 10
+    j = np.arange(n)
+    e = np.exp(2j * np.pi * 37 * j / n).astype(np.complex64)[None]
+    got = _run(gb, e)[0]
+    want = np.zeros(n)
+    want[37] = 1
+    assert np.max(np.abs(got - want)) < 1e-6
+
+
+@pytest.mark.parametrize("log2n", [8, 12, 14, 16, 20, 24])
+def test_full_size_sweep_sampled(gb, log2n):
+    """The 1D sweep configuration: batch * N = 2^26 complex64.  Sampled whole
+    transforms against the oracle; every transform checked by the round trip
+    inverse(forward(x)) = x."""
+    import torch
+
+    n = 1 << log2n
+    batch = (1 << 26) // n
+    x = synth.complex_uniform((batch, n), 2, log2n)
+    t = torch.from_numpy(x).cuda()
+    c = gb.fft(t)
+    picks = sorted({0, batch - 1, batch // 2, (7 * batch) // 11})[: (2 if log2n >= 22 else 4)]
+    ref = oracle.fft(x[picks].astype(np.complex128))
+    assert max_rel_l2(c[picks].cpu().numpy(), ref, axes=-1) <= tol_fp32(n)
+    f = gb.ifft(c)
+    err = torch.sqrt(torch.sum(torch.abs(f - t) ** 2, dim=-1) / torch.sum(torch.abs(t) ** 2, dim=-1))
+    assert float(err.max()) <= 2 * tol_fp32(n)
+
+
+def test_fp64_full_size_sampled(gb):
+    """FP64 variant of the sweep: N = 2^20, batch 64."""
+    import torch
+
+    n, batch = 1 << 20, 64
+    x = synth.complex_uniform((batch, n), 2, 20, 64)
+    t = torch.from_numpy(x).cuda().to(torch.complex128)
+    c = gb.fft(t)
+    picks = [0, 33, 63]
+    ref = oracle.fft(x[picks].astype(np.complex128))
+    assert max_rel_l2(c[picks].cpu().numpy(), ref, axes=-1) <= FP64_TOL
+    bins = np.array([0, 1, 12345, n // 2, n - 1])
+    direct = oracle.dft_bins(x[5].astype(np.complex128), bins)
+    assert np.max(np.abs(c[5].cpu().numpy()[bins] - direct)) <= 1e-12 * np.sqrt(n) * np.max(np.abs(direct))
