@@ -79,7 +79,15 @@ typedef enum {
     GBFFT_OPT_IMAGES_PER_CHUNK = 4,
     /* 1 = record a CUDA event pair around every kernel launch of this plan
      * (read with gbfft_plan_profile_read); 0 (default) = off. */
-    GBFFT_OPT_PROFILE = 5
+    GBFFT_OPT_PROFILE = 5,
+    /* 2D: 1 = reserve the second spectrum buffer that the filter gradient of
+     * fft2_filter_ifft2_backward needs (doubles the spectrum part of the
+     * workspace); 0 (default) = forward and grad_img only. */
+    GBFFT_OPT_ENABLE_BACKWARD = 6,
+    /* 2D tuning: columns per thread block in the fused column pass,
+     * 0 = default for the size, v = 1..5 requests 2^(v-1) columns; a width
+     * whose block does not fit the GPU returns GBFFT_ERR_INVALID_VALUE. */
+    GBFFT_OPT_COLS_TILE = 7
 } gbfft_option;
 
 /* Stages reported by gbfft_plan_profile_read. */
@@ -139,12 +147,16 @@ int fft_inverse(gbfft_plan_t plan, const void *in, void *out, gbfft_stream_t str
  * value.  img == out is allowed. */
 int fft2_filter_ifft2(gbfft_plan_t plan, const float *img, const float *H, float *out, gbfft_stream_t stream);
 
-/* Adjoint of fft2_filter_ifft2 for an upstream gradient grad_out = dL/dout:
+/* Adjoint of fft2_filter_ifft2 for an upstream gradient grad_out = dL/dout
+ * (derived from Sec. 4's 2D-DFT and Sec. 5's filter; the paper has no
+ * gradient):
  *   grad_img_b = Re(ifft2(H . fft2(grad_out_b)))          (same shape as img)
  *   grad_H[k]  = N M sum_b Re(conj(fft2(grad_out_b)[k]) fft2(img_b)[k])
- * with per-axis spectra; H is shared (h_batch_stride must be 0) and grad_H
- * (rows x cols float32) is overwritten with the sum over the batch.
- * grad_img may be NULL (then only grad_H is produced) and so may grad_H. */
+ * with per-axis spectra.  grad_H (rows x cols float32) is overwritten with
+ * the sum over the batch; it needs a shared H (h_batch_stride 0,
+ * else GBFFT_ERR_UNSUPPORTED) and GBFFT_OPT_ENABLE_BACKWARD set before the
+ * workspace is bound (else GBFFT_ERR_WORKSPACE).  grad_img or grad_H may be
+ * NULL to skip that output; img may be NULL when grad_H is. */
 int fft2_filter_ifft2_backward(gbfft_plan_t plan, const float *img, const float *H, const float *grad_out,
                                float *grad_img, float *grad_H, gbfft_stream_t stream);
 

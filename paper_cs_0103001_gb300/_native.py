@@ -35,6 +35,8 @@ OPT_H_BATCH_STRIDE = 2
 OPT_PRECISION = 3
 OPT_IMAGES_PER_CHUNK = 4
 OPT_PROFILE = 5
+OPT_ENABLE_BACKWARD = 6
+OPT_COLS_TILE = 7
 
 # gbfft_stage
 STAGES = ("fft1d", "fourstep_a", "fourstep_b", "rows_fwd", "cols_filter", "rows_inv", "cols_grad", "twiddles")

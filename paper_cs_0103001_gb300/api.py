@@ -163,11 +163,13 @@ def ifft(c: torch.Tensor) -> torch.Tensor:
     return _plan1d(c).inverse(c)
 
 
-def _plan2d(img: torch.Tensor, per_image_H: bool) -> Plan2D:
+def _plan2d(img: torch.Tensor, per_image_H: bool, backward: bool = False) -> Plan2D:
     rows, cols = img.shape[-2:]
     batch = img.numel() // (rows * cols)
     opts = {nat.OPT_H_BATCH_STRIDE: rows * cols if per_image_H else 0}
-    key = ("2d", rows, cols, batch, per_image_H, img.device)
+    if backward:
+        opts[nat.OPT_ENABLE_BACKWARD] = 1
+    key = ("2d", rows, cols, batch, per_image_H, backward, img.device)
     return _cached(key, lambda: Plan2D(rows, cols, batch, img.device, opts))
 
 
@@ -199,8 +201,8 @@ class _FilterFn(torch.autograd.Function):
     def backward(ctx, grad_out):
         img, H = ctx.saved_tensors
         g = grad_out.contiguous()
-        plan = _plan2d(img, ctx.per_image)
         need_img, need_H = ctx.needs_input_grad[0], ctx.needs_input_grad[1]
+        plan = _plan2d(img, ctx.per_image, backward=need_H and not ctx.per_image)
         if ctx.per_image:
             if need_H:
                 raise NotImplementedError("grad of a per-image filter stack is not supported; share one H")

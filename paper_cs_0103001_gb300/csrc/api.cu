@@ -41,12 +41,13 @@ struct gbfft_plan {
     int log2n = 0;               // 1D length
     int log2r = 0, log2c = 0;    // 2D rows (N) and cols (M)
     int64_t opt_scale_conv = 0, opt_h_stride = 0, opt_precision = 0, opt_chunk = 0, opt_profile = 0;
+    int64_t opt_backward = 0, opt_cols_variant = 0;
     // workspace
     char *ws = nullptr;
     size_t ws_bytes = 0;
     bool bound = false;
     // layout (byte offsets into ws)
-    size_t off_tw0 = 0, off_tw1 = 0, off_tw2 = 0, off_buf = 0, need = 0;
+    size_t off_tw0 = 0, off_tw1 = 0, off_tw2 = 0, off_buf = 0, off_buf2 = 0, need = 0;
     int64_t chunk = 0;           // transforms (1D four-step) or images (2D) per workspace chunk
     int fs_l1 = 0, fs_l2 = 0;    // four-step split
     std::vector<ProfRec> prof;
@@ -117,6 +118,8 @@ void layout(gbfft_plan *p) {
         if (chunk > 65535) chunk = 65535;
         p->chunk = chunk;
         off = align_up(off + (size_t)chunk * img_bytes);
+        p->off_buf2 = off;  // second spectrum buffer for the adjoint (G's spectra)
+        if (p->opt_backward) off = align_up(off + (size_t)chunk * img_bytes);
     }
     p->need = off;
 }
@@ -270,6 +273,16 @@ int fft_plan_set_option(gbfft_plan_t p, int key, int64_t value) {
             if (value != 0 && value != 1) return GBFFT_ERR_INVALID_VALUE;
             p->opt_profile = value;
             return GBFFT_OK;
+        case GBFFT_OPT_COLS_TILE:
+            if (p->kind != KIND_2D || !cols_variant_valid(1 << p->log2r, 1 << p->log2c, (int)value))
+                return GBFFT_ERR_INVALID_VALUE;
+            p->opt_cols_variant = value;
+            return GBFFT_OK;
+        case GBFFT_OPT_ENABLE_BACKWARD:
+            if (p->kind != KIND_2D || (value != 0 && value != 1)) return GBFFT_ERR_INVALID_VALUE;
+            p->opt_backward = value;
+            layout(p);
+            return GBFFT_OK;
         default: return GBFFT_ERR_INVALID_VALUE;
     }
 }
@@ -341,7 +354,8 @@ int fft2_filter_ifft2(gbfft_plan_t p, const float *img, const float *H, float *o
         rc = launch(p, GBFFT_STAGE_ROWS_FWD, s, [&] { return launch_rows_fwd(ib, spec, rows, cols, nb, twc, s); });
         if (rc) return rc;
         rc = launch(p, GBFFT_STAGE_COLS, s, [&] {
-            return launch_cols_filter(spec, hb, p->opt_h_stride, rows, cols, nb, scale, twr, s);
+            return launch_cols_filter(spec, hb, p->opt_h_stride, rows, cols, nb, scale, twr, s,
+                                      (int)p->opt_cols_variant);
         });
         if (rc) return rc;
         rc = launch(p, GBFFT_STAGE_ROWS_INV, s, [&] { return launch_rows_inv(spec, ob, rows, cols, nb, twc, s); });
@@ -352,14 +366,54 @@ int fft2_filter_ifft2(gbfft_plan_t p, const float *img, const float *H, float *o
 
 int fft2_filter_ifft2_backward(gbfft_plan_t p, const float *img, const float *H, const float *grad_out,
                                float *grad_img, float *grad_H, gbfft_stream_t stream) {
-    (void)img;
-    (void)H;
-    (void)grad_out;
-    (void)grad_img;
-    (void)grad_H;
-    (void)stream;
-    if (!p) return GBFFT_ERR_NULL;
-    return GBFFT_ERR_UNSUPPORTED;
+    int rc = check_plan_ready(p);
+    if (rc) return rc;
+    if (p->kind != KIND_2D) return GBFFT_ERR_INVALID_VALUE;
+    if (!H || !grad_out || (grad_H && !img)) return GBFFT_ERR_NULL;
+    if (misaligned(img) || misaligned(H) || misaligned(grad_out) || misaligned(grad_img) || misaligned(grad_H))
+        return GBFFT_ERR_MISALIGNED;
+    if (!grad_img && !grad_H) return GBFFT_OK;
+    if (grad_H && p->opt_h_stride != 0) return GBFFT_ERR_UNSUPPORTED;  // grad of a shared filter only
+    if (grad_H && !p->opt_backward) return GBFFT_ERR_WORKSPACE;        // needs the second spectrum buffer
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int rows = 1 << p->log2r, cols = 1 << p->log2c;
+    const int64_t np = (int64_t)rows * cols;
+    const float scale = (float)(1.0 / (double)np);
+    void *spec_x = p->ws + p->off_buf, *spec_g = p->ws + p->off_buf2;
+    const void *twc = p->ws + p->off_tw0, *twr = p->ws + p->off_tw1;
+    for (int64_t b0 = 0; b0 < p->batch; b0 += p->chunk) {
+        const int nb = (int)((p->batch - b0 < p->chunk) ? p->batch - b0 : p->chunk);
+        const float *gb = grad_out + b0 * np;
+        if (!grad_H) {  // grad_img only: the pipeline itself, applied to grad_out
+            const float *hb = H + b0 * p->opt_h_stride;
+            rc = launch(p, GBFFT_STAGE_ROWS_FWD, s, [&] { return launch_rows_fwd(gb, spec_x, rows, cols, nb, twc, s); });
+            if (rc) return rc;
+            rc = launch(p, GBFFT_STAGE_COLS, s, [&] {
+                return launch_cols_filter(spec_x, hb, p->opt_h_stride, rows, cols, nb, scale, twr, s,
+                                          (int)p->opt_cols_variant);
+            });
+            if (rc) return rc;
+            rc = launch(p, GBFFT_STAGE_ROWS_INV, s,
+                        [&] { return launch_rows_inv(spec_x, grad_img + b0 * np, rows, cols, nb, twc, s); });
+            if (rc) return rc;
+            continue;
+        }
+        rc = launch(p, GBFFT_STAGE_ROWS_FWD, s,
+                    [&] { return launch_rows_fwd(img + b0 * np, spec_x, rows, cols, nb, twc, s); });
+        if (rc) return rc;
+        rc = launch(p, GBFFT_STAGE_ROWS_FWD, s, [&] { return launch_rows_fwd(gb, spec_g, rows, cols, nb, twc, s); });
+        if (rc) return rc;
+        rc = launch(p, GBFFT_STAGE_COLS_GRAD, s, [&] {
+            return launch_cols_grad(spec_x, spec_g, H, grad_H, rows, cols, nb, scale, b0 > 0 ? 1 : 0, twr, s);
+        });
+        if (rc) return rc;
+        if (grad_img) {
+            rc = launch(p, GBFFT_STAGE_ROWS_INV, s,
+                        [&] { return launch_rows_inv(spec_g, grad_img + b0 * np, rows, cols, nb, twc, s); });
+            if (rc) return rc;
+        }
+    }
+    return GBFFT_OK;
 }
 
 int fft_plan_destroy(gbfft_plan_t p) {

@@ -186,6 +186,18 @@ template <int R, int DIR, typename C> __device__ __forceinline__ void dft(C *a) 
 
 template <typename C> __device__ __forceinline__ C ldg_c(const C *p) { return __ldg(p); }
 
+// ----------------------------------------------- asynchronous copies ------
+// cp.async (global -> shared without a register round trip); `bytes` is 4, 8
+// or 16 and both addresses must be aligned to it.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *smem_dst, const void *gmem_src) {
+    static_assert(BYTES == 4 || BYTES == 8 || BYTES == 16, "cp.async size");
+    const unsigned d = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(d), "l"(gmem_src), "n"(BYTES) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 // ------------------------------------------------------- one pass ---------
 // sm: this transform's exchange buffer, element x at sm[pad16(x) * S]
 // (S > 1 interleaves S transforms element by element).

@@ -42,8 +42,16 @@ cudaError_t launch_fourstep_b(const void *tmp, void *out, int log2n, long long b
 // column 0 of a half spectrum row packs (DC, Nyquist) as (re, im)).
 cudaError_t launch_rows_fwd(const float *img, void *spec, int rows, int cols, int nimg, const void *tw_cols,
                             cudaStream_t s);
+// `variant` selects the column-tile width (0 = default; see cols.cu).
 cudaError_t launch_cols_filter(void *spec, const float *H, long long h_stride, int rows, int cols, int nimg,
-                               float scale, const void *tw_rows, cudaStream_t s);
+                               float scale, const void *tw_rows, cudaStream_t s, int variant = 0);
+int cols_variants();
+bool cols_variant_valid(int rows, int cols, int variant);
+// Adjoint column pass (cols_grad.cu): per column tile, loop over nimg images of
+// spec_x / spec_g, accumulate grad_H = scale * sum Re(conj(W G) W x) (added to
+// grad_H's contents when `accumulate`), and filter + inverse-transform spec_g.
+cudaError_t launch_cols_grad(const void *spec_x, void *spec_g, const float *H, float *grad_H, int rows, int cols,
+                             int nimg, float scale, int accumulate, const void *tw_rows, cudaStream_t s);
 cudaError_t launch_rows_inv(const void *spec, float *out, int rows, int cols, int nimg, const void *tw_cols,
                             cudaStream_t s);
 
