@@ -44,6 +44,15 @@ typedef struct CUstream_st *gbfft_stream_t;
 
 typedef struct gbfft_plan *gbfft_plan_t;
 
+/* Device-resident pointers of one image of a batched call (see
+ * fft2_filter_ifft2_batched): its float32 image, filter and output, each
+ * rows x cols row-major, 16-byte aligned. */
+typedef struct {
+    const float *img;
+    const float *H;
+    float *out;
+} gbfft_image_ptrs;
+
 typedef enum {
     GBFFT_C64 = 1,  /* complex64: float32 pairs; 2D images are float32 */
     GBFFT_C128 = 2, /* complex128: float64 pairs; 2D images are float64 */
@@ -69,7 +78,8 @@ typedef enum {
      * of fft2_filter_ifft2 is the same under both. */
     GBFFT_OPT_SCALE_CONVENTION = 1,
     /* Element stride between the filters of consecutive images in a batch:
-     * 0 (default) shares one H; rows*cols gives each image its own. */
+     * 0 (default) shares one H; rows*cols gives each image its own.  Changes
+     * fft_plan_workspace_bytes (one prepared filter per image in a chunk). */
     GBFFT_OPT_H_BATCH_STRIDE = 2,
     /* Arithmetic of the butterflies: 0 = FP32 (default for C64),
      * 1 = split-BF16 tensor-core radix-16 stages (C64 only). */
@@ -84,10 +94,14 @@ typedef enum {
      * fft2_filter_ifft2_backward needs (doubles the spectrum part of the
      * workspace); 0 (default) = forward and grad_img only. */
     GBFFT_OPT_ENABLE_BACKWARD = 6,
-    /* 2D tuning: columns per thread block in the fused column pass,
-     * 0 = default for the size, v = 1..5 requests 2^(v-1) columns; a width
-     * whose block does not fit the GPU returns GBFFT_ERR_INVALID_VALUE. */
-    GBFFT_OPT_COLS_TILE = 7
+    /* Batched plans: thread blocks per SM of each persistent stage launch
+     * (0 = as many as fit, the default; fft_plan_autotune sets it per stage).
+     * fft_plan_get_option returns the three stages packed 8 bits each. */
+    GBFFT_OPT_BLOCKS_PER_SM = 7,
+    /* Batched plans: 1 (default) = capture the three stage launches in a CUDA
+     * graph on the first call and replay it while the image-pointer array and
+     * the launch shapes stay the same; 0 = plain launches. */
+    GBFFT_OPT_USE_GRAPH = 8
 } gbfft_option;
 
 /* Stages reported by gbfft_plan_profile_read. */
@@ -100,7 +114,8 @@ typedef enum {
     GBFFT_STAGE_ROWS_INV = 5,  /* 2D row pass, inverse (half spectra -> real rows) */
     GBFFT_STAGE_COLS_GRAD = 6, /* 2D fused column pass of the adjoint (grad_H) */
     GBFFT_STAGE_TWIDDLES = 7,  /* twiddle-table generation (bind time) */
-    GBFFT_STAGE_COUNT = 8
+    GBFFT_STAGE_GRAPH = 8,     /* one replay of a batched plan's captured graph */
+    GBFFT_STAGE_COUNT = 9
 } gbfft_stage;
 
 /* ---- plans --------------------------------------------------------------- */
@@ -159,6 +174,30 @@ int fft2_filter_ifft2(gbfft_plan_t plan, const float *img, const float *H, float
  * NULL to skip that output; img may be NULL when grad_H is. */
 int fft2_filter_ifft2_backward(gbfft_plan_t plan, const float *img, const float *H, const float *grad_out,
                                float *grad_img, float *grad_H, gbfft_stream_t stream);
+
+/* Batched plan for the Sec. 5 pipeline over `count` images of uneven sizes,
+ * image i being rows[i] x cols[i] (powers of two, 16 <= rows, cols <= 4096),
+ * each with its own filter of the same shape.  All images' spectra live in
+ * the workspace at once (fft_plan_workspace_bytes); binding it uploads the
+ * image table and the per-stage work lists and builds the twiddle tables. */
+int fft2_batched_plan_create(int count, const int64_t *rows, const int64_t *cols, gbfft_plan_t *out);
+
+/* Run a batched plan: out_i = Re(ifft2(H_i . fft2(img_i))) for every image.
+ * `images` is a DEVICE array of `count` gbfft_image_ptrs (caller-owned; the
+ * kernels read it when they run).  Three persistent launches, one per stage
+ * (forward rows, fused columns, inverse rows), each over a largest-first work
+ * list of all images; with GBFFT_OPT_USE_GRAPH they are captured once in a
+ * CUDA graph (on a private stream) and replayed on `stream`. */
+int fft2_filter_ifft2_batched(gbfft_plan_t plan, const gbfft_image_ptrs *images, gbfft_stream_t stream);
+
+/* Tune a plan's launch shapes by timing candidates on `stream` (blocking).
+ * Batched plans: blocks per SM of each stage, `args` = the device image
+ * array of fft2_filter_ifft2_batched (the outputs are written).  Other plans
+ * have nothing to tune and return GBFFT_OK. */
+int fft_plan_autotune(gbfft_plan_t plan, const void *args, gbfft_stream_t stream);
+
+/* Read back an option (GBFFT_OPT_IMAGES_PER_CHUNK gives the chunk in use). */
+int fft_plan_get_option(gbfft_plan_t plan, int key, int64_t *value);
 
 /* Destroy a plan (host state only; the workspace belongs to the caller). */
 int fft_plan_destroy(gbfft_plan_t plan);

@@ -36,10 +36,12 @@ OPT_PRECISION = 3
 OPT_IMAGES_PER_CHUNK = 4
 OPT_PROFILE = 5
 OPT_ENABLE_BACKWARD = 6
-OPT_COLS_TILE = 7
+OPT_BLOCKS_PER_SM = 7
+OPT_USE_GRAPH = 8
 
 # gbfft_stage
-STAGES = ("fft1d", "fourstep_a", "fourstep_b", "rows_fwd", "cols_filter", "rows_inv", "cols_grad", "twiddles")
+STAGES = ("fft1d", "fourstep_a", "fourstep_b", "rows_fwd", "cols_filter", "rows_inv", "cols_grad", "twiddles",
+          "graph")
 
 # every exported symbol with (restype, argtypes)
 _P = ctypes.c_void_p
@@ -56,6 +58,10 @@ SIGNATURES = {
     "fft2_filter_ifft2": (_INT, [_P, _P, _P, _P, _P]),
     "fft2_filter_ifft2_backward": (_INT, [_P, _P, _P, _P, _P, _P, _P]),
     "fft_plan_destroy": (_INT, [_P]),
+    "fft2_batched_plan_create": (_INT, [_INT, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_P)]),
+    "fft2_filter_ifft2_batched": (_INT, [_P, _P, _P]),
+    "fft_plan_autotune": (_INT, [_P, _P, _P]),
+    "fft_plan_get_option": (_INT, [_P, _INT, ctypes.POINTER(_I64)]),
     "gbfft_status_string": (ctypes.c_char_p, [_INT]),
     "gbfft_last_cuda_error": (_INT, []),
     "gbfft_plan_profile_read": (_INT, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64), _INT]),

@@ -3,9 +3,12 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <map>
 #include <new>
 #include <vector>
 
+#include "batched.h"
 #include "gbfft.h"
 #include "internal.h"
 
@@ -20,7 +23,7 @@ struct ProfRec {
     cudaEvent_t a, b;
 };
 
-enum PlanKind { KIND_1D = 1, KIND_2D = 2 };
+enum PlanKind { KIND_1D = 1, KIND_2D = 2, KIND_BATCH = 3 };
 
 constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
@@ -41,16 +44,30 @@ struct gbfft_plan {
     int log2n = 0;               // 1D length
     int log2r = 0, log2c = 0;    // 2D rows (N) and cols (M)
     int64_t opt_scale_conv = 0, opt_h_stride = 0, opt_precision = 0, opt_chunk = 0, opt_profile = 0;
-    int64_t opt_backward = 0, opt_cols_variant = 0;
+    int64_t opt_backward = 0;
     // workspace
     char *ws = nullptr;
     size_t ws_bytes = 0;
     bool bound = false;
     // layout (byte offsets into ws)
     size_t off_tw0 = 0, off_tw1 = 0, off_tw2 = 0, off_buf = 0, off_buf2 = 0, need = 0;
+    size_t off_hs = 0, off_beta = 0, off_grad = 0;  // 2D: prepared filter, beta, adjoint sums
     int64_t chunk = 0;           // transforms (1D four-step) or images (2D) per workspace chunk
     int fs_l1 = 0, fs_l2 = 0;    // four-step split
     std::vector<ProfRec> prof;
+    // batched plans (KIND_BATCH)
+    std::vector<BatchImage> bimgs;
+    std::vector<BatchItem> bitems[3];
+    std::map<int, size_t> tw_off;  // twiddle table per distinct length
+    size_t off_bimgs = 0, off_bitems[3] = {0, 0, 0};
+    size_t bsmem[3] = {0, 0, 0};
+    int64_t opt_bps[3] = {0, 0, 0};  // blocks per SM per stage (0 = as many as fit)
+    int64_t opt_graph = 1;
+    cudaStream_t cap_stream = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    const void *graph_ptrs = nullptr;
+    int graph_grid[3] = {0, 0, 0};
 };
 
 namespace {
@@ -69,9 +86,43 @@ int64_t l2_budget_bytes() {
     return 48ll << 20;
 }
 
+void layout_batched(gbfft_plan *p) {
+    size_t off = 0;
+    p->off_bimgs = off;
+    off = align_up(off + p->bimgs.size() * sizeof(BatchImage));
+    for (int st = 0; st < 3; ++st) {
+        p->off_bitems[st] = off;
+        off = align_up(off + p->bitems[st].size() * sizeof(BatchItem));
+    }
+    p->tw_off.clear();
+    for (const BatchImage &im : p->bimgs) {
+        for (int len : {im.cols, im.rows}) {
+            if (p->tw_off.count(len)) continue;
+            p->tw_off[len] = off;
+            off = align_up(off + (size_t)len * 8);
+        }
+    }
+    for (BatchImage &im : p->bimgs) {
+        const size_t half_px = (size_t)im.rows * (im.cols / 2);
+        im.twc_off = (long long)p->tw_off[im.cols];
+        im.twr_off = (long long)p->tw_off[im.rows];
+        im.spec_off = (long long)off;
+        off = align_up(off + half_px * 8);
+        im.hs_off = (long long)off;
+        off = align_up(off + half_px * 4);
+        im.beta_off = (long long)off;
+        off = align_up(off + (size_t)im.rows * 4);
+    }
+    p->need = off;
+}
+
 // Compute the workspace layout for the current options.
 void layout(gbfft_plan *p) {
     size_t off = 0;
+    if (p->kind == KIND_BATCH) {
+        layout_batched(p);
+        return;
+    }
     if (p->kind == KIND_1D) {
         const int64_t n = int64_t(1) << p->log2n;
         if (p->log2n <= max_single_log2(p)) {
@@ -107,8 +158,8 @@ void layout(gbfft_plan *p) {
         p->off_tw1 = off;  // column transforms (length rows)
         off = align_up(off + (size_t)rows * 8);
         p->off_tw2 = off;
-        p->off_buf = off;
-        const int64_t img_bytes = rows * (cols / 2) * 8;
+        const int64_t half_px = rows * (cols / 2);
+        const int64_t img_bytes = half_px * 8;
         int64_t chunk = p->opt_chunk;
         if (chunk <= 0) {
             chunk = l2_budget_bytes() / img_bytes;
@@ -117,9 +168,20 @@ void layout(gbfft_plan *p) {
         if (chunk > p->batch) chunk = p->batch;
         if (chunk > 65535) chunk = 65535;
         p->chunk = chunk;
+        const int64_t nfilt = p->opt_h_stride != 0 ? chunk : 1;  // prepared filters held at once
+        p->off_hs = off;
+        off = align_up(off + (size_t)nfilt * half_px * 4);
+        p->off_beta = off;
+        off = align_up(off + (size_t)nfilt * rows * 4);
+        p->off_buf = off;
         off = align_up(off + (size_t)chunk * img_bytes);
-        p->off_buf2 = off;  // second spectrum buffer for the adjoint (G's spectra)
-        if (p->opt_backward) off = align_up(off + (size_t)chunk * img_bytes);
+        p->off_buf2 = off;  // G's spectra and the filter-gradient sums (adjoint only)
+        p->off_grad = off;
+        if (p->opt_backward) {
+            off = align_up(off + (size_t)chunk * img_bytes);
+            p->off_grad = off;
+            off = align_up(off + (size_t)(cols / 2 + 1) * rows * 4);
+        }
     }
     p->need = off;
 }
@@ -187,6 +249,43 @@ int run_1d(gbfft_plan *p, const void *in, void *out, int dir, cudaStream_t s) {
         if (rc) return rc;
     }
     return GBFFT_OK;
+}
+
+int sm_count() {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return 0;
+    return n;
+}
+
+// Grid of a batched stage: blocks per SM (option, else as many as fit) x SMs.
+int batched_grid(gbfft_plan *p, int st, cudaError_t *err) {
+    int fit = 0;
+    *err = batch_max_blocks_per_sm(st, p->bsmem[st], &fit);
+    if (*err != cudaSuccess) return 0;
+    if (fit < 1) fit = 1;
+    int bps = p->opt_bps[st] > 0 ? (int)p->opt_bps[st] : fit;
+    if (bps > fit) bps = fit;
+    return bps * sm_count();
+}
+
+cudaError_t batched_launch_all(gbfft_plan *p, const gbfft_image_ptrs *ptrs, cudaStream_t s, const int *grid) {
+    const BatchImage *imgs = reinterpret_cast<const BatchImage *>(p->ws + p->off_bimgs);
+    for (int st = 0; st < 3; ++st) {
+        const BatchItem *items = reinterpret_cast<const BatchItem *>(p->ws + p->off_bitems[st]);
+        cudaError_t e = launch_batched_stage(st, grid[st], p->bsmem[st], imgs, items, (int)p->bitems[st].size(), ptrs,
+                                             p->ws, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+void drop_graph(gbfft_plan *p) {
+    if (p->graph_exec) cudaGraphExecDestroy(p->graph_exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    p->graph_exec = nullptr;
+    p->graph = nullptr;
+    p->graph_ptrs = nullptr;
 }
 
 }  // namespace
@@ -259,6 +358,7 @@ int fft_plan_set_option(gbfft_plan_t p, int key, int64_t value) {
         case GBFFT_OPT_H_BATCH_STRIDE:
             if (p->kind != KIND_2D || value < 0) return GBFFT_ERR_INVALID_VALUE;
             p->opt_h_stride = value;
+            layout(p);
             return GBFFT_OK;
         case GBFFT_OPT_PRECISION:
             if (value != 0) return value == 1 ? GBFFT_ERR_UNSUPPORTED : GBFFT_ERR_INVALID_VALUE;
@@ -273,10 +373,15 @@ int fft_plan_set_option(gbfft_plan_t p, int key, int64_t value) {
             if (value != 0 && value != 1) return GBFFT_ERR_INVALID_VALUE;
             p->opt_profile = value;
             return GBFFT_OK;
-        case GBFFT_OPT_COLS_TILE:
-            if (p->kind != KIND_2D || !cols_variant_valid(1 << p->log2r, 1 << p->log2c, (int)value))
-                return GBFFT_ERR_INVALID_VALUE;
-            p->opt_cols_variant = value;
+        case GBFFT_OPT_BLOCKS_PER_SM:
+            if (p->kind != KIND_BATCH || value < 0 || value > 64) return GBFFT_ERR_INVALID_VALUE;
+            p->opt_bps[0] = p->opt_bps[1] = p->opt_bps[2] = value;
+            drop_graph(p);
+            return GBFFT_OK;
+        case GBFFT_OPT_USE_GRAPH:
+            if (p->kind != KIND_BATCH || (value != 0 && value != 1)) return GBFFT_ERR_INVALID_VALUE;
+            p->opt_graph = value;
+            drop_graph(p);
             return GBFFT_OK;
         case GBFFT_OPT_ENABLE_BACKWARD:
             if (p->kind != KIND_2D || (value != 0 && value != 1)) return GBFFT_ERR_INVALID_VALUE;
@@ -314,10 +419,23 @@ int fft_plan_bind_workspace(gbfft_plan_t p, void *workspace, size_t bytes, gbfft
                 return e;
             });
         }
-    } else {
+    } else if (p->kind == KIND_2D) {
         rc = launch(p, GBFFT_STAGE_TWIDDLES, s, [&] {
             cudaError_t e = launch_twiddles(p->ws + p->off_tw0, 1 << p->log2c, false, s);
             if (e == cudaSuccess) e = launch_twiddles(p->ws + p->off_tw1, 1 << p->log2r, false, s);
+            return e;
+        });
+    } else {
+        drop_graph(p);
+        rc = launch(p, GBFFT_STAGE_TWIDDLES, s, [&] {
+            // tables live in plan-owned host vectors, so the copies may complete later
+            cudaError_t e = cudaMemcpyAsync(p->ws + p->off_bimgs, p->bimgs.data(),
+                                            p->bimgs.size() * sizeof(BatchImage), cudaMemcpyHostToDevice, s);
+            for (int st = 0; st < 3 && e == cudaSuccess; ++st)
+                e = cudaMemcpyAsync(p->ws + p->off_bitems[st], p->bitems[st].data(),
+                                    p->bitems[st].size() * sizeof(BatchItem), cudaMemcpyHostToDevice, s);
+            for (const auto &kv : p->tw_off)
+                if (e == cudaSuccess) e = launch_twiddles(p->ws + kv.second, kv.first, false, s);
             return e;
         });
     }
@@ -334,6 +452,37 @@ int fft_inverse(gbfft_plan_t p, const void *in, void *out, gbfft_stream_t stream
     return run_1d(p, in, out, +1, reinterpret_cast<cudaStream_t>(stream));
 }
 
+// One chunk of the Sec. 5 pipeline: row pass (+ filter preparation), fused
+// column pass, inverse row pass.
+static int pipeline_chunk(gbfft_plan *p, const float *img, const float *H, float *out, int nb, bool first,
+                          cudaStream_t s) {
+    const int rows = 1 << p->log2r, cols = 1 << p->log2c;
+    const int64_t half_px = (int64_t)rows * (cols / 2);
+    const bool per_image = p->opt_h_stride != 0;
+    RowsFwdArgs a;
+    a.img = img;
+    a.spec = p->ws + p->off_buf;
+    a.rows = rows;
+    a.cols = cols;
+    a.nimg = nb;
+    a.H = H;
+    a.hs = reinterpret_cast<float *>(p->ws + p->off_hs);
+    a.beta = reinterpret_cast<float *>(p->ws + p->off_beta);
+    a.h_stride = p->opt_h_stride;
+    a.filter_mode = per_image ? 2 : (first ? 1 : 0);  // a shared filter is prepared once per call
+    a.scale = (float)(1.0 / ((double)rows * cols));
+    a.tw = p->ws + p->off_tw0;
+    int rc = launch(p, GBFFT_STAGE_ROWS_FWD, s, [&] { return launch_rows_fwd(a, s); });
+    if (rc) return rc;
+    rc = launch(p, GBFFT_STAGE_COLS, s, [&] {
+        return launch_cols_filter(a.spec, a.hs, a.beta, per_image ? half_px : 0, per_image ? rows : 0, rows, cols, nb,
+                                  p->ws + p->off_tw1, s);
+    });
+    if (rc) return rc;
+    return launch(p, GBFFT_STAGE_ROWS_INV, s,
+                  [&] { return launch_rows_inv(a.spec, out, rows, cols, nb, p->ws + p->off_tw0, s); });
+}
+
 int fft2_filter_ifft2(gbfft_plan_t p, const float *img, const float *H, float *out, gbfft_stream_t stream) {
     int rc = check_plan_ready(p);
     if (rc) return rc;
@@ -341,24 +490,10 @@ int fft2_filter_ifft2(gbfft_plan_t p, const float *img, const float *H, float *o
     if (!img || !H || !out) return GBFFT_ERR_NULL;
     if (misaligned(img) || misaligned(H) || misaligned(out)) return GBFFT_ERR_MISALIGNED;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    const int rows = 1 << p->log2r, cols = 1 << p->log2c;
-    const int64_t np = (int64_t)rows * cols;
-    const float scale = (float)(1.0 / (double)np);
-    void *spec = p->ws + p->off_buf;
-    const void *twc = p->ws + p->off_tw0, *twr = p->ws + p->off_tw1;
+    const int64_t np = (int64_t)(1 << p->log2r) << p->log2c;
     for (int64_t b0 = 0; b0 < p->batch; b0 += p->chunk) {
         const int nb = (int)((p->batch - b0 < p->chunk) ? p->batch - b0 : p->chunk);
-        const float *ib = img + b0 * np;
-        float *ob = out + b0 * np;
-        const float *hb = H + b0 * p->opt_h_stride;
-        rc = launch(p, GBFFT_STAGE_ROWS_FWD, s, [&] { return launch_rows_fwd(ib, spec, rows, cols, nb, twc, s); });
-        if (rc) return rc;
-        rc = launch(p, GBFFT_STAGE_COLS, s, [&] {
-            return launch_cols_filter(spec, hb, p->opt_h_stride, rows, cols, nb, scale, twr, s,
-                                      (int)p->opt_cols_variant);
-        });
-        if (rc) return rc;
-        rc = launch(p, GBFFT_STAGE_ROWS_INV, s, [&] { return launch_rows_inv(spec, ob, rows, cols, nb, twc, s); });
+        rc = pipeline_chunk(p, img + b0 * np, H + b0 * p->opt_h_stride, out + b0 * np, nb, b0 == 0, s);
         if (rc) return rc;
     }
     return GBFFT_OK;
@@ -373,51 +508,243 @@ int fft2_filter_ifft2_backward(gbfft_plan_t p, const float *img, const float *H,
     if (misaligned(img) || misaligned(H) || misaligned(grad_out) || misaligned(grad_img) || misaligned(grad_H))
         return GBFFT_ERR_MISALIGNED;
     if (!grad_img && !grad_H) return GBFFT_OK;
-    if (grad_H && p->opt_h_stride != 0) return GBFFT_ERR_UNSUPPORTED;  // grad of a shared filter only
-    if (grad_H && !p->opt_backward) return GBFFT_ERR_WORKSPACE;        // needs the second spectrum buffer
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     const int rows = 1 << p->log2r, cols = 1 << p->log2c;
     const int64_t np = (int64_t)rows * cols;
-    const float scale = (float)(1.0 / (double)np);
+    if (!grad_H) {  // grad_img only: the pipeline itself, applied to grad_out
+        for (int64_t b0 = 0; b0 < p->batch; b0 += p->chunk) {
+            const int nb = (int)((p->batch - b0 < p->chunk) ? p->batch - b0 : p->chunk);
+            rc = pipeline_chunk(p, grad_out + b0 * np, H + b0 * p->opt_h_stride, grad_img + b0 * np, nb, b0 == 0, s);
+            if (rc) return rc;
+        }
+        return GBFFT_OK;
+    }
+    if (p->opt_h_stride != 0) return GBFFT_ERR_UNSUPPORTED;  // grad of a shared filter only
+    if (!p->opt_backward) return GBFFT_ERR_WORKSPACE;         // needs the second spectrum buffer
     void *spec_x = p->ws + p->off_buf, *spec_g = p->ws + p->off_buf2;
-    const void *twc = p->ws + p->off_tw0, *twr = p->ws + p->off_tw1;
+    float *hs = reinterpret_cast<float *>(p->ws + p->off_hs);
+    float *beta = reinterpret_cast<float *>(p->ws + p->off_beta);
+    float *grad_T = reinterpret_cast<float *>(p->ws + p->off_grad);
+    const float scale = (float)(1.0 / (double)np);
     for (int64_t b0 = 0; b0 < p->batch; b0 += p->chunk) {
         const int nb = (int)((p->batch - b0 < p->chunk) ? p->batch - b0 : p->chunk);
-        const float *gb = grad_out + b0 * np;
-        if (!grad_H) {  // grad_img only: the pipeline itself, applied to grad_out
-            const float *hb = H + b0 * p->opt_h_stride;
-            rc = launch(p, GBFFT_STAGE_ROWS_FWD, s, [&] { return launch_rows_fwd(gb, spec_x, rows, cols, nb, twc, s); });
-            if (rc) return rc;
-            rc = launch(p, GBFFT_STAGE_COLS, s, [&] {
-                return launch_cols_filter(spec_x, hb, p->opt_h_stride, rows, cols, nb, scale, twr, s,
-                                          (int)p->opt_cols_variant);
-            });
-            if (rc) return rc;
-            rc = launch(p, GBFFT_STAGE_ROWS_INV, s,
-                        [&] { return launch_rows_inv(spec_x, grad_img + b0 * np, rows, cols, nb, twc, s); });
-            if (rc) return rc;
-            continue;
-        }
-        rc = launch(p, GBFFT_STAGE_ROWS_FWD, s,
-                    [&] { return launch_rows_fwd(img + b0 * np, spec_x, rows, cols, nb, twc, s); });
+        RowsFwdArgs a;
+        a.img = img + b0 * np;
+        a.spec = spec_x;
+        a.rows = rows;
+        a.cols = cols;
+        a.nimg = nb;
+        a.H = H;
+        a.hs = hs;
+        a.beta = beta;
+        a.h_stride = 0;
+        a.filter_mode = b0 == 0 ? 1 : 0;
+        a.scale = scale;
+        a.tw = p->ws + p->off_tw0;
+        rc = launch(p, GBFFT_STAGE_ROWS_FWD, s, [&] { return launch_rows_fwd(a, s); });
         if (rc) return rc;
-        rc = launch(p, GBFFT_STAGE_ROWS_FWD, s, [&] { return launch_rows_fwd(gb, spec_g, rows, cols, nb, twc, s); });
+        a.img = grad_out + b0 * np;
+        a.spec = spec_g;
+        a.filter_mode = 0;
+        rc = launch(p, GBFFT_STAGE_ROWS_FWD, s, [&] { return launch_rows_fwd(a, s); });
         if (rc) return rc;
         rc = launch(p, GBFFT_STAGE_COLS_GRAD, s, [&] {
-            return launch_cols_grad(spec_x, spec_g, H, grad_H, rows, cols, nb, scale, b0 > 0 ? 1 : 0, twr, s);
+            return launch_cols_grad(spec_x, spec_g, hs, beta, grad_T, rows, cols, nb, scale, b0 > 0 ? 1 : 0,
+                                    p->ws + p->off_tw1, s);
         });
         if (rc) return rc;
         if (grad_img) {
-            rc = launch(p, GBFFT_STAGE_ROWS_INV, s,
-                        [&] { return launch_rows_inv(spec_g, grad_img + b0 * np, rows, cols, nb, twc, s); });
+            rc = launch(p, GBFFT_STAGE_ROWS_INV, s, [&] {
+                return launch_rows_inv(spec_g, grad_img + b0 * np, rows, cols, nb, p->ws + p->off_tw0, s);
+            });
             if (rc) return rc;
         }
     }
+    return launch(p, GBFFT_STAGE_COLS_GRAD, s, [&] { return launch_grad_scatter(grad_T, grad_H, rows, cols, s); });
+}
+
+int fft2_batched_plan_create(int count, const int64_t *rows, const int64_t *cols, gbfft_plan_t *out) {
+    if (!out) return GBFFT_ERR_NULL;
+    *out = nullptr;
+    if (!rows || !cols) return GBFFT_ERR_NULL;
+    if (count < 1) return GBFFT_ERR_INVALID_SIZE;
+    gbfft_plan *p = new (std::nothrow) gbfft_plan();
+    if (!p) return GBFFT_ERR_UNSUPPORTED;
+    p->kind = KIND_BATCH;
+    p->dtype = GBFFT_C64;
+    p->batch = count;
+    struct Costed {
+        double cost;
+        BatchItem it;
+    };
+    std::vector<Costed> work[3];
+    for (int i = 0; i < count; ++i) {
+        const int lr = ilog2_exact(rows[i]), lc = ilog2_exact(cols[i]);
+        if (lr < kBatchMinLog2 || lr > kBatchMaxLog2 || lc < kBatchMinLog2 || lc > kBatchMaxLog2) {
+            delete p;
+            return GBFFT_ERR_INVALID_SIZE;
+        }
+        BatchImage im = {};
+        im.rows = (int)rows[i];
+        im.cols = (int)cols[i];
+        im.log2r = lr;
+        im.log2c = lc;
+        int g = batch_row_pairs(im.cols);
+        if (g > im.rows / 2) g = im.rows / 2;
+        im.log2g = ilog2_exact(g);
+        im.scale = (float)(1.0 / ((double)im.rows * im.cols));
+        p->bimgs.push_back(im);
+        const int nrow = (im.rows / 2) / g;
+        const double crow = 2.0 * g * im.cols * lc;
+        for (int bx = 0; bx < nrow; ++bx) {
+            work[0].push_back({crow, {i, bx}});
+            work[2].push_back({crow, {i, bx}});
+        }
+        const int w = batch_col_width(im.rows);
+        const int ncol = (im.cols / 2 + w - 1) / w;
+        const double ccol = 2.0 * w * im.rows * lr;
+        for (int bx = 0; bx < ncol; ++bx) work[1].push_back({ccol, {i, bx}});
+        p->bsmem[0] = std::max(p->bsmem[0], batch_row_smem(im.cols));
+        p->bsmem[1] = std::max(p->bsmem[1], batch_col_smem(im.rows));
+    }
+    p->bsmem[2] = p->bsmem[0];
+    for (int st = 0; st < 3; ++st) {
+        // largest first; equal costs keep image order
+        std::stable_sort(work[st].begin(), work[st].end(),
+                         [](const Costed &a, const Costed &b) { return a.cost > b.cost; });
+        for (const Costed &c : work[st]) p->bitems[st].push_back(c.it);
+    }
+    layout(p);
+    *out = p;
     return GBFFT_OK;
+}
+
+int fft2_filter_ifft2_batched(gbfft_plan_t p, const gbfft_image_ptrs *images, gbfft_stream_t stream) {
+    int rc = check_plan_ready(p);
+    if (rc) return rc;
+    if (p->kind != KIND_BATCH) return GBFFT_ERR_INVALID_VALUE;
+    if (!images) return GBFFT_ERR_NULL;
+    if (misaligned(images)) return GBFFT_ERR_MISALIGNED;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int grid[3];
+    cudaError_t e = cudaSuccess;
+    for (int st = 0; st < 3; ++st) {
+        grid[st] = batched_grid(p, st, &e);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    if (!p->opt_graph) {
+        for (int st = 0; st < 3; ++st) {
+            const int stage = st == 0 ? GBFFT_STAGE_ROWS_FWD : st == 1 ? GBFFT_STAGE_COLS : GBFFT_STAGE_ROWS_INV;
+            rc = launch(p, stage, s, [&] {
+                return launch_batched_stage(st, grid[st], p->bsmem[st],
+                                            reinterpret_cast<const BatchImage *>(p->ws + p->off_bimgs),
+                                            reinterpret_cast<const BatchItem *>(p->ws + p->off_bitems[st]),
+                                            (int)p->bitems[st].size(), images, p->ws, s);
+            });
+            if (rc) return rc;
+        }
+        return GBFFT_OK;
+    }
+    if (!p->graph_exec || p->graph_ptrs != images || p->graph_grid[0] != grid[0] || p->graph_grid[1] != grid[1] ||
+        p->graph_grid[2] != grid[2]) {
+        drop_graph(p);
+        if (!p->cap_stream && (e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
+            return cuda_fail(e);
+        e = cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e);
+        cudaError_t le = batched_launch_all(p, images, p->cap_stream, grid);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(p->cap_stream, &g);
+        if (le != cudaSuccess || e != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            return cuda_fail(le != cudaSuccess ? le : e);
+        }
+        p->graph = g;
+        e = cudaGraphInstantiate(&p->graph_exec, p->graph, 0);
+        if (e != cudaSuccess) {
+            drop_graph(p);
+            return cuda_fail(e);
+        }
+        p->graph_ptrs = images;
+        for (int st = 0; st < 3; ++st) p->graph_grid[st] = grid[st];
+    }
+    return launch(p, GBFFT_STAGE_GRAPH, s, [&] { return cudaGraphLaunch(p->graph_exec, s); });
+}
+
+int fft_plan_autotune(gbfft_plan_t p, const void *args, gbfft_stream_t stream) {
+    if (!p) return GBFFT_ERR_NULL;
+    if (p->kind != KIND_BATCH) return GBFFT_OK;  // nothing tunable beyond the defaults
+    int rc = check_plan_ready(p);
+    if (rc) return rc;
+    if (!args) return GBFFT_ERR_NULL;
+    const gbfft_image_ptrs *images = static_cast<const gbfft_image_ptrs *>(args);
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    if (e != cudaSuccess) return cuda_fail(e);
+    const int nsm = sm_count();
+    int grid[3];
+    for (int st = 0; st < 3 && e == cudaSuccess; ++st) {
+        int fit = 0;
+        e = batch_max_blocks_per_sm(st, p->bsmem[st], &fit);
+        if (fit < 1) fit = 1;
+        for (int q = 0; q < 3; ++q) grid[q] = (p->opt_bps[q] > 0 ? (int)p->opt_bps[q] : fit) * nsm;
+        float best = 1e30f;
+        int best_bps = fit;
+        for (int bps = 1; bps <= fit && e == cudaSuccess; ++bps) {
+            grid[st] = bps * nsm;
+            float total = 0.f;
+            for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+                for (int q = 0; q < 3 && e == cudaSuccess; ++q) {
+                    if (q == st) e = cudaEventRecord(a, s);
+                    if (e == cudaSuccess)
+                        e = launch_batched_stage(q, grid[q], p->bsmem[q],
+                                                 reinterpret_cast<const BatchImage *>(p->ws + p->off_bimgs),
+                                                 reinterpret_cast<const BatchItem *>(p->ws + p->off_bitems[q]),
+                                                 (int)p->bitems[q].size(), images, p->ws, s);
+                    if (q == st && e == cudaSuccess) e = cudaEventRecord(b, s);
+                }
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventSynchronize(b);
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+                if (rep > 0) total += ms;  // first repetition warms up
+            }
+            if (e == cudaSuccess && total < best) {
+                best = total;
+                best_bps = bps;
+            }
+        }
+        p->opt_bps[st] = best_bps;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    drop_graph(p);
+    return e == cudaSuccess ? GBFFT_OK : cuda_fail(e);
+}
+
+int fft_plan_get_option(gbfft_plan_t p, int key, int64_t *value) {
+    if (!p || !value) return GBFFT_ERR_NULL;
+    switch (key) {
+        case GBFFT_OPT_SCALE_CONVENTION: *value = p->opt_scale_conv; return GBFFT_OK;
+        case GBFFT_OPT_H_BATCH_STRIDE: *value = p->opt_h_stride; return GBFFT_OK;
+        case GBFFT_OPT_PRECISION: *value = p->opt_precision; return GBFFT_OK;
+        case GBFFT_OPT_IMAGES_PER_CHUNK: *value = p->chunk; return GBFFT_OK;
+        case GBFFT_OPT_PROFILE: *value = p->opt_profile; return GBFFT_OK;
+        case GBFFT_OPT_ENABLE_BACKWARD: *value = p->opt_backward; return GBFFT_OK;
+        case GBFFT_OPT_BLOCKS_PER_SM:
+            // three stages packed 8 bits each: forward rows | columns << 8 | inverse rows << 16
+            *value = p->opt_bps[0] | (p->opt_bps[1] << 8) | (p->opt_bps[2] << 16);
+            return GBFFT_OK;
+        case GBFFT_OPT_USE_GRAPH: *value = p->opt_graph; return GBFFT_OK;
+        default: return GBFFT_ERR_INVALID_VALUE;
+    }
 }
 
 int fft_plan_destroy(gbfft_plan_t p) {
     if (!p) return GBFFT_ERR_NULL;
+    drop_graph(p);
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     for (auto &r : p->prof) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);

@@ -1,0 +1,169 @@
+// batched.cu — the Sec. 5 pipeline over many images of uneven power-of-two
+// sizes, each with its own filter, in three persistent kernel launches.
+//
+// A batched plan fixes the image shapes.  At bind time it uploads an image
+// table (shape, workspace offsets) and one work list per stage: the thread
+// blocks the regular kernels would launch for every image, (image, block)
+// pairs, sorted by decreasing cost.  Each stage is one persistent launch of a
+// few blocks per SM; block i takes items i, i + grid, i + 2 grid, ... (a
+// fixed assignment: no counters to reset, the same work split every call),
+// dispatching on the item's size to the same block bodies as the regular
+// kernels (rows_impl.cuh, cols_impl.cuh).  The three launches can be captured
+// once in a CUDA graph and replayed.  Blocks per SM are a tunable of the plan.
+#include "batched.h"
+#include "cols_impl.cuh"
+#include "internal.h"
+#include "rows_impl.cuh"
+
+namespace gbfft {
+
+template <int L>
+__device__ __forceinline__ void fwd_case(const BatchImage &im, const gbfft_image_ptrs &pp, char *ws, int bx,
+                                         unsigned char *sm) {
+    rows_fwd_body<(1 << L)>(pp.img, reinterpret_cast<float2 *>(ws + im.spec_off), pp.H,
+                            reinterpret_cast<float *>(ws + im.hs_off), reinterpret_cast<float *>(ws + im.beta_off),
+                            im.rows, im.log2g, true, im.scale, reinterpret_cast<const float2 *>(ws + im.twc_off), bx,
+                            sm);
+}
+
+template <int L>
+__device__ __forceinline__ void inv_case(const BatchImage &im, const gbfft_image_ptrs &pp, char *ws, int bx,
+                                         unsigned char *sm) {
+    rows_inv_body<(1 << L)>(reinterpret_cast<const float2 *>(ws + im.spec_off), pp.out, im.rows, im.log2g,
+                            reinterpret_cast<const float2 *>(ws + im.twc_off), bx, sm);
+}
+
+template <int L>
+__device__ __forceinline__ void cols_case(const BatchImage &im, char *ws, int bx, unsigned char *sm) {
+    cols_body<(1 << L)>(reinterpret_cast<float2 *>(ws + im.spec_off), reinterpret_cast<const float *>(ws + im.hs_off),
+                        reinterpret_cast<const float *>(ws + im.beta_off), im.cols, im.log2g,
+                        reinterpret_cast<const float2 *>(ws + im.twr_off), bx, sm);
+}
+
+#define GBFFT_BATCH_SIZES(X) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12)
+
+__global__ void __launch_bounds__(kBatchRowThreads, 2)
+    k_batched_rows_fwd(const BatchImage *__restrict__ imgs, const BatchItem *__restrict__ items, int nitems,
+                       const gbfft_image_ptrs *__restrict__ ptrs, char *ws) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
+        const BatchItem it = items[i];
+        const BatchImage im = imgs[it.img];
+        const gbfft_image_ptrs pp = ptrs[it.img];
+        __syncthreads();  // shared memory of the previous item is free
+        switch (im.log2c) {
+#define GBFFT_C(L) \
+    case L: fwd_case<L>(im, pp, ws, it.bx, smraw); break;
+            GBFFT_BATCH_SIZES(GBFFT_C)
+#undef GBFFT_C
+            default: break;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBatchColThreads, 2)
+    k_batched_cols(const BatchImage *__restrict__ imgs, const BatchItem *__restrict__ items, int nitems, char *ws) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
+        const BatchItem it = items[i];
+        const BatchImage im = imgs[it.img];
+        __syncthreads();
+        switch (im.log2r) {
+#define GBFFT_C(L) \
+    case L: cols_case<L>(im, ws, it.bx, smraw); break;
+            GBFFT_BATCH_SIZES(GBFFT_C)
+#undef GBFFT_C
+            default: break;
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBatchRowThreads, 2)
+    k_batched_rows_inv(const BatchImage *__restrict__ imgs, const BatchItem *__restrict__ items, int nitems,
+                       const gbfft_image_ptrs *__restrict__ ptrs, char *ws) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    for (int i = blockIdx.x; i < nitems; i += gridDim.x) {
+        const BatchItem it = items[i];
+        const BatchImage im = imgs[it.img];
+        const gbfft_image_ptrs pp = ptrs[it.img];
+        __syncthreads();
+        switch (im.log2c) {
+#define GBFFT_C(L) \
+    case L: inv_case<L>(im, pp, ws, it.bx, smraw); break;
+            GBFFT_BATCH_SIZES(GBFFT_C)
+#undef GBFFT_C
+            default: break;
+        }
+    }
+}
+
+// ---- host side: shapes of the block bodies -------------------------------
+
+int batch_row_pairs(int cols) {
+    switch (ilog2(cols)) {
+#define GBFFT_C(L) \
+    case L: return RowCfg<(1 << L)>::PPC;
+        GBFFT_BATCH_SIZES(GBFFT_C)
+#undef GBFFT_C
+        default: return 0;
+    }
+}
+
+size_t batch_row_smem(int cols) {
+    switch (ilog2(cols)) {
+#define GBFFT_C(L) \
+    case L: return RowCfg<(1 << L)>::SMEM;
+        GBFFT_BATCH_SIZES(GBFFT_C)
+#undef GBFFT_C
+        default: return 0;
+    }
+}
+
+int batch_col_width(int rows) {
+    switch (ilog2(rows)) {
+#define GBFFT_C(L) \
+    case L: return ColCfg<(1 << L)>::W;
+        GBFFT_BATCH_SIZES(GBFFT_C)
+#undef GBFFT_C
+        default: return 0;
+    }
+}
+
+size_t batch_col_smem(int rows) {
+    switch (ilog2(rows)) {
+#define GBFFT_C(L) \
+    case L: return ColCfg<(1 << L)>::SMEM;
+        GBFFT_BATCH_SIZES(GBFFT_C)
+#undef GBFFT_C
+        default: return 0;
+    }
+}
+
+static_assert(RowCfg<16>::THREADS == kBatchRowThreads && RowCfg<4096>::THREADS == kBatchRowThreads,
+              "row bodies of every batched size use the same block");
+static_assert(ColCfg<16>::THREADS == kBatchColThreads && ColCfg<4096>::THREADS == kBatchColThreads,
+              "column bodies of every batched size use the same block");
+
+cudaError_t batch_max_blocks_per_sm(int stage, size_t smem, int *blocks) {
+    const void *k = stage == 0   ? (const void *)k_batched_rows_fwd
+                    : stage == 1 ? (const void *)k_batched_cols
+                                 : (const void *)k_batched_rows_inv;
+    const int threads = stage == 1 ? kBatchColThreads : kBatchRowThreads;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, threads, smem);
+}
+
+cudaError_t launch_batched_stage(int stage, int grid, size_t smem, const BatchImage *imgs, const BatchItem *items,
+                                 int nitems, const gbfft_image_ptrs *ptrs, char *ws, cudaStream_t s) {
+    if (nitems <= 0) return cudaSuccess;
+    if (grid > nitems) grid = nitems;
+    switch (stage) {
+        case 0: k_batched_rows_fwd<<<grid, kBatchRowThreads, smem, s>>>(imgs, items, nitems, ptrs, ws); break;
+        case 1: k_batched_cols<<<grid, kBatchColThreads, smem, s>>>(imgs, items, nitems, ws); break;
+        default: k_batched_rows_inv<<<grid, kBatchRowThreads, smem, s>>>(imgs, items, nitems, ptrs, ws); break;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace gbfft

@@ -9,184 +9,204 @@
 // even: the half spectrum k = 0..M/2 gives every bin, the mirror bin
 // (-u, -k) receiving the same value.
 //
-// One thread block owns W adjacent half-spectrum columns and loops over the
-// images of the chunk: column FFT of x's and of G's row spectra, accumulate
-// Re(conj(WG) WX) in registers (no atomics; the order of the sum is fixed),
-// then filter G's column by s Hs and inverse-transform it in place for the
-// inverse row pass, exactly as the forward column pass does.  The packed
-// column 0 (DC in re, Nyquist in im) is split into its two real-column
-// spectra P = (Q + conj Q[-u]) / 2 and R = (Q - conj Q[-u]) / (2i) first.
+// One group of T threads owns one half-spectrum column k (slot order, see
+// layout.cuh) and loops over the images of the chunk: column FFT of x's and
+// of G's row spectra, accumulate Re(conj(WG) WX) in registers (no atomics;
+// the order of the sum is fixed), then filter G's column with the prepared
+// s * Hs and inverse-transform it in place for the inverse row pass, exactly
+// as the forward column pass does.  The packed column 0 (DC in re, Nyquist in
+// im) is split into its two real-column spectra P = (Q + conj Q[-u]) / 2 and
+// R = (Q - conj Q[-u]) / (2i) first.  Sums go to a slot-order buffer
+// [M/2 + 1][N] (column M/2 holds the Nyquist column) that k_grad_scatter
+// finally writes out row-major, mirror bins included.
 #include "fft_core.cuh"
 #include "internal.h"
+#include "layout.cuh"
 
 namespace gbfft {
 
 template <int N> struct GradCfg {
     static constexpr int E = N < 16 ? N : 16;
     static constexpr int T = N / E;
-    // shared memory per block: exchange buffers for x and G (2 x 8.5 B), the
-    // running sums (4 B) and the filter tile H[u][k], H[-u][-k] (2 x 4 B) per
-    // element and column, plus one N-float sum for the packed column
-    static constexpr int WMAX_SMEM = 4096 / N;
-    static constexpr int WMAX_THR = 512 / T;
-    static constexpr int WMAX0 = WMAX_SMEM < WMAX_THR ? WMAX_SMEM : WMAX_THR;
-    static constexpr int WMAX = WMAX0 > 64 ? 64 : (WMAX0 < 1 ? 1 : WMAX0);
-    static constexpr size_t SMEM = 2 * (size_t)padded_len(N) * WMAX * 8 + (size_t)N * WMAX * (4 + 8) + (size_t)N * 4;
-    static constexpr bool VALID = SMEM <= 227 * 1024;
-    static constexpr int THREADS = WMAX * T;
+    static constexpr int W = T >= 256 ? 1 : 256 / T;
+    static constexpr int THREADS = W * T;
+    static constexpr size_t SMEM = 2 * (size_t)W * padded_len(N) * sizeof(float2);
 };
+
+template <int N, int E, int T>
+__device__ __forceinline__ int grad_slot(int t, int e, int log2g) {
+    int p, side;
+    if (e < E / 2) {
+        p = t + T * e;
+        side = 0;
+    } else {
+        p = (e == E / 2 && t == 0) ? 0 : N - (t + T * e);
+        side = 1;
+    }
+    return ((p >> log2g) << (log2g + 1)) + (side << log2g) + (p & ((1 << log2g) - 1));
+}
 
 template <int N>
 __global__ void __launch_bounds__(GradCfg<N>::THREADS)
-    k_cols_grad(const float2 *spec_x, float2 *spec_g, const float *__restrict__ H, float *grad_H, int M, int nimg,
-                float scale, int accumulate, const float2 *__restrict__ tw) {
+    k_cols_grad(const float2 *spec_x, float2 *spec_g, const float *__restrict__ hs, const float *__restrict__ beta,
+                float *grad_T, int M, int nimg, int log2g, float scale, int accumulate,
+                const float2 *__restrict__ tw) {
     typedef GradCfg<N> K;
-    constexpr int E = K::E, T = K::T, W = K::WMAX;
+    constexpr int E = K::E, T = K::T, W = K::W;
     extern __shared__ __align__(16) unsigned char smraw[];
-    float2 *smx = reinterpret_cast<float2 *>(smraw);
-    float2 *smg = smx + padded_len(N) * W;
-    // running sums of Re(conj(WG) WX) per thread and element: bin (u, k)
-    // [packed column: (u, 0)] and, for the packed column only, (u, M/2)
-    float *acc = reinterpret_cast<float *>(smg + padded_len(N) * W);
-    float *hd = acc + N * W;  // H[u][k] at u*W + w (shared by every image)
-    float *hm = hd + N * W;   // H[-u][-k]
-    float *acc2 = hm + N * W; // packed column only, at u
-    const int w = threadIdx.x % W;
-    const int t = threadIdx.x / W;
+    const int w = threadIdx.x / T;
+    const int t = threadIdx.x - w * T;
+    float2 *exx = reinterpret_cast<float2 *>(smraw) + w * padded_len(N);
+    float2 *exg = reinterpret_cast<float2 *>(smraw) + (W + w) * padded_len(N);
     const int half = M >> 1;
     const int k0 = blockIdx.x * W + w;
     const bool active = k0 < half;
     const int k = active ? k0 : 0;
-    const int km = (M - k) & (M - 1);
-    const bool packed = active && k0 == 0;  // the packed DC/Nyquist column (block 0, w = 0)
 
-    const int tid = threadIdx.x;
-    constexpr int NT = W * T;
-    const int k0b = blockIdx.x * W;
-#pragma unroll
-    for (int j = 0; j < E; ++j) {
-        const int idx = tid + j * NT;
-        const int u = idx / W, ww = idx % W;
-        const int kc = (k0b + ww < half) ? k0b + ww : 0;
-        const int um = (N - u) & (N - 1), kmc = (M - kc) & (M - 1);
-        cp_async<4>(hd + idx, H + (size_t)u * M + kc);
-        cp_async<4>(hm + idx, H + (size_t)um * M + kmc);
-        acc[idx] = 0.f;
-    }
-    cp_async_commit();
-    if (packed) {
-#pragma unroll
-        for (int e = 0; e < E; ++e) acc2[t + T * e] = 0.f;
-    }
-    cp_async_wait_all();
-
-    for (int b = 0; b < nimg; ++b) {
-        const float2 *cx = spec_x + (size_t)b * N * half + k;
-        float2 *cg = spec_g + (size_t)b * N * half + k;
-        float2 v[E];
-        // x's column spectrum, parked in natural order in its exchange buffer
-#pragma unroll
-        for (int e = 0; e < E; ++e) v[e] = active ? cx[(t + T * e) * half] : make_float2(0.f, 0.f);
-        fft_regs<N, E, -1>(v, smx + w, tw, t, W);
-        __syncthreads();
-#pragma unroll
-        for (int e = 0; e < E; ++e) smx[pad16(t + T * e) * W + w] = v[e];
-        // G's column spectrum in registers
-#pragma unroll
-        for (int e = 0; e < E; ++e) v[e] = active ? cg[(t + T * e) * half] : make_float2(0.f, 0.f);
-        fft_regs<N, E, -1>(v, smg + w, tw, t, W);
-        if (blockIdx.x == 0) {  // the packed column needs bin -u of G's spectrum too
-            __syncthreads();
-#pragma unroll
-            for (int e = 0; e < E; ++e) smg[pad16(t + T * e) * W + w] = v[e];
-        }
-        __syncthreads();
-        if (!packed) {
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const int u = t + T * e;
-                const float2 vx = smx[pad16(u) * W + w];
-                acc[u * W + w] += v[e].x * vx.x + v[e].y * vx.y;
-                v[e] = cscale(v[e], 0.5f * scale * (hd[u * W + w] + hm[u * W + w]));
-            }
-        } else {
-#pragma unroll
-            for (int e = 0; e < E; ++e) {
-                const int u = t + T * e;
-                const int um = (N - u) & (N - 1);
-                const float2 vx = smx[pad16(u) * W];
-                const float2 qx = smx[pad16(um) * W], qg = smg[pad16(um) * W];
-                // P = (Q + conj Qm)/2, R = (Q - conj Qm)/(2i)
-                const float2 px = make_float2(0.5f * (vx.x + qx.x), 0.5f * (vx.y - qx.y));
-                const float2 rx = make_float2(0.5f * (vx.y + qx.y), 0.5f * (qx.x - vx.x));
-                const float2 pg = make_float2(0.5f * (v[e].x + qg.x), 0.5f * (v[e].y - qg.y));
-                const float2 rg = make_float2(0.5f * (v[e].y + qg.y), 0.5f * (qg.x - v[e].x));
-                acc[u * W] += pg.x * px.x + pg.y * px.y;
-                acc2[u] += rg.x * rx.x + rg.y * rx.y;
-                const float h0 = 0.5f * (hd[u * W] + hm[u * W]);
-                const float h1 = 0.5f * (H[u * M + half] + H[um * M + half]);
-                const float alpha = 0.5f * scale * (h0 + h1), beta = 0.5f * scale * (h0 - h1);
-                v[e] = make_float2(alpha * v[e].x + beta * qg.x, alpha * v[e].y - beta * qg.y);
-            }
-        }
-        fft_regs<N, E, 1>(v, smg + w, tw, t, W);
-        if (active) {
-#pragma unroll
-            for (int e = 0; e < E; ++e) cg[(t + T * e) * half] = v[e];
-        }
-        __syncthreads();  // smx is rewritten by the next image
-    }
-    if (!active) return;
+    int sl[E];
+    float h[E], acc[E], acc2[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) {
-        const int u = t + T * e;
-        const int um = (N - u) & (N - 1);
-        if (!packed) {
-            float g = scale * acc[u * W + w];
-            if (accumulate) g += grad_H[u * M + k];
-            grad_H[u * M + k] = g;
-            grad_H[um * M + km] = g;  // even: same value at the mirror bin
-        } else {
-            float g0 = scale * acc[u * W], g1 = scale * acc2[u];
-            if (accumulate) {
-                g0 += grad_H[u * M];
-                g1 += grad_H[u * M + half];
+        sl[e] = grad_slot<N, E, T>(t, e, log2g);
+        h[e] = hs[(size_t)k * N + sl[e]];
+        acc[e] = 0.f;
+        acc2[e] = 0.f;
+    }
+
+    for (int b = 0; b < nimg; ++b) {
+        const float2 *cx = spec_x + (size_t)b * half * N + (size_t)k * N;
+        float2 *cg = spec_g + (size_t)b * half * N + (size_t)k * N;
+        float2 vx[E], vg[E];
+#pragma unroll
+        for (int e = 0; e < E; ++e) vx[e] = active ? cx[sl[e]] : make_float2(0.f, 0.f);
+        fft_regs<N, E, -1>(vx, exx, tw, t);
+#pragma unroll
+        for (int e = 0; e < E; ++e) vg[e] = active ? cg[sl[e]] : make_float2(0.f, 0.f);
+        fft_regs<N, E, -1>(vg, exg, tw, t);
+        if (blockIdx.x == 0) {  // column 0 needs bin -u of both spectra (uniform per block)
+            __syncthreads();
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                exx[pad16(t + T * e)] = vx[e];
+                exg[pad16(t + T * e)] = vg[e];
             }
-            grad_H[u * M] = g0;
-            grad_H[u * M + half] = g1;
+            __syncthreads();
+        }
+        if (k != 0) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                acc[e] += vg[e].x * vx[e].x + vg[e].y * vx[e].y;
+                vg[e] = cscale(vg[e], h[e]);
+            }
+        } else {
+#pragma unroll
+            for (int e = 0; e < E; ++e) {
+                const int um = (N - (t + T * e)) & (N - 1);
+                const float2 qx = exx[pad16(um)], qg = exg[pad16(um)];
+                // P = (Q + conj Qm)/2, R = (Q - conj Qm)/(2i)
+                const float2 px = make_float2(0.5f * (vx[e].x + qx.x), 0.5f * (vx[e].y - qx.y));
+                const float2 rx = make_float2(0.5f * (vx[e].y + qx.y), 0.5f * (qx.x - vx[e].x));
+                const float2 pg = make_float2(0.5f * (vg[e].x + qg.x), 0.5f * (vg[e].y - qg.y));
+                const float2 rg = make_float2(0.5f * (vg[e].y + qg.y), 0.5f * (qg.x - vg[e].x));
+                acc[e] += pg.x * px.x + pg.y * px.y;
+                acc2[e] += rg.x * rx.x + rg.y * rx.y;
+                const float bt = beta[sl[e]];
+                vg[e] = make_float2(h[e] * vg[e].x + bt * qg.x, h[e] * vg[e].y - bt * qg.y);
+            }
+        }
+        fft_regs<N, E, 1>(vg, exg, tw, t);
+        if (active) {
+#pragma unroll
+            for (int e = 0; e < E; ++e) cg[sl[e]] = vg[e];
+        }
+    }
+    if (!active) return;
+    float *gcol = grad_T + (size_t)k * N;
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        float g = scale * acc[e];
+        if (accumulate) g += gcol[sl[e]];
+        gcol[sl[e]] = g;
+    }
+    if (k == 0) {
+        float *ncol = grad_T + (size_t)half * N;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            float g = scale * acc2[e];
+            if (accumulate) g += ncol[sl[e]];
+            ncol[sl[e]] = g;
+        }
+    }
+}
+
+// grad_T [M/2 + 1][N] (slot order) -> grad_H [N][M] row-major, mirror bins filled.
+__global__ void __launch_bounds__(256)
+    k_grad_scatter(const float *__restrict__ grad_T, float *__restrict__ grad_H, int N, int M, int log2g) {
+    __shared__ float tile[32][33];
+    const int half = M >> 1;
+    const int kb = blockIdx.x * 32, sb = blockIdx.y * 32;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    for (int i = ty; i < 32; i += 8) {
+        const int k = kb + i, s = sb + tx;
+        tile[i][tx] = (k <= half && s < N) ? grad_T[(size_t)k * N + s] : 0.f;
+    }
+    __syncthreads();
+    for (int i = ty; i < 32; i += 8) {
+        const int s = sb + i, k = kb + tx;
+        if (s >= N || k > half) continue;
+        const int u = row_of_slot(s, N, log2g);
+        const float g = tile[tx][i];
+        if (k == 0 || k == half) {
+            grad_H[(size_t)u * M + k] = g;
+        } else {
+            grad_H[(size_t)u * M + k] = g;
+            grad_H[(size_t)((N - u) & (N - 1)) * M + (M - k)] = g;
         }
     }
 }
 
 template <int N>
-static cudaError_t run_grad(const void *spec_x, void *spec_g, const float *H, float *grad_H, int cols, int nimg,
-                            float scale, int accumulate, const void *tw, cudaStream_t s) {
+static cudaError_t run_grad(const void *spec_x, void *spec_g, const float *hs, const float *beta, float *grad_T,
+                            int cols, int nimg, int log2g, float scale, int accumulate, const void *tw,
+                            cudaStream_t s) {
     typedef GradCfg<N> K;
-    constexpr int W = K::WMAX;
-    const int half = cols / 2;
-    const size_t smem = K::SMEM;
-    if (!K::VALID) return cudaErrorInvalidConfiguration;
     auto kern = k_cols_grad<N>;
-    if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (K::SMEM > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::SMEM);
         if (e != cudaSuccess) return e;
     }
-    dim3 grid((half + W - 1) / W);
-    kern<<<grid, W * K::T, smem, s>>>(static_cast<const float2 *>(spec_x), static_cast<float2 *>(spec_g), H, grad_H,
-                                      cols, nimg, scale, accumulate, static_cast<const float2 *>(tw));
+    const int half = cols / 2;
+    dim3 grid((half + K::W - 1) / K::W);
+    kern<<<grid, K::THREADS, K::SMEM, s>>>(static_cast<const float2 *>(spec_x), static_cast<float2 *>(spec_g), hs,
+                                           beta, grad_T, cols, nimg, log2g, scale, accumulate,
+                                           static_cast<const float2 *>(tw));
     return cudaGetLastError();
 }
 
-cudaError_t launch_cols_grad(const void *spec_x, void *spec_g, const float *H, float *grad_H, int rows, int cols,
-                             int nimg, float scale, int accumulate, const void *tw_rows, cudaStream_t s) {
+cudaError_t launch_cols_grad(const void *spec_x, void *spec_g, const float *hs, const float *beta, float *grad_T,
+                             int rows, int cols, int nimg, float scale, int accumulate, const void *tw_rows,
+                             cudaStream_t s) {
+    int g = rows_pairs_per_block(cols);
+    if (g > rows / 2) g = rows / 2;
+    const int log2g = ilog2(g);
     switch (ilog2(rows)) {
-#define GBFFT_CASE(L) \
-    case L: return run_grad<(1 << L)>(spec_x, spec_g, H, grad_H, cols, nimg, scale, accumulate, tw_rows, s);
+#define GBFFT_CASE(L)                                                                                      \
+    case L:                                                                                                \
+        return run_grad<(1 << L)>(spec_x, spec_g, hs, beta, grad_T, cols, nimg, log2g, scale, accumulate, \
+                                  tw_rows, s);
         GBFFT_CASE(1) GBFFT_CASE(2) GBFFT_CASE(3) GBFFT_CASE(4) GBFFT_CASE(5) GBFFT_CASE(6) GBFFT_CASE(7)
         GBFFT_CASE(8) GBFFT_CASE(9) GBFFT_CASE(10) GBFFT_CASE(11) GBFFT_CASE(12) GBFFT_CASE(13)
 #undef GBFFT_CASE
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_grad_scatter(const float *grad_T, float *grad_H, int rows, int cols, cudaStream_t s) {
+    int g = rows_pairs_per_block(cols);
+    if (g > rows / 2) g = rows / 2;
+    dim3 grid((cols / 2 + 1 + 31) / 32, (rows + 31) / 32);
+    k_grad_scatter<<<grid, dim3(32, 8), 0, s>>>(grad_T, grad_H, rows, cols, ilog2(g));
+    return cudaGetLastError();
 }
 
 }  // namespace gbfft

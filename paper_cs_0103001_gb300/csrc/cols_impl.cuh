@@ -1,0 +1,113 @@
+// cols_impl.cuh — the fused column pass of the Sec. 5 pipeline.
+//
+// The row pass leaves, per image, the row half spectra column-major in slot
+// order (layout.cuh) and the prepared filter s * Hs[u][k] in the same order.
+// One group of T threads owns one half-spectrum column k and runs, without
+// leaving the chip:
+//   column FFT (length N = rows, Eq. E2 direction, unscaled)
+//   x s * Hs[u, k]        (the filter of Sec. 5 with the 2D scale s = 1/(N M))
+//   column inverse FFT    (Eq. E3, unscaled)
+// and writes the column back in place.  Column and filter are contiguous in
+// memory, so every warp access is a full line; one HBM (or L2) read and one
+// write of the spectrum, no transpose kernel.
+//
+// Real part.  The pipeline's output Re(ifft2(H . F)) equals ifft2(Hs . F) with
+// Hs[k] = (H[k] + H[-k]) / 2, because F (the spectrum of a real image) is
+// Hermitian: the real part keeps only the even part of the filter.
+//
+// Column 0 packs two real-row spectra (DC in re, Nyquist in im, see rows.cu):
+// q[x] = a[x] + i c[x].  Its column FFT Q splits as P = (Q + conj Q[-u]) / 2 and
+// R = (Q - conj Q[-u]) / (2i); filtering P by Hs[u,0] and R by Hs[u,M/2] and
+// recombining gives
+//   Q'[u] = alpha Q[u] + beta conj(Q[-u]),  alpha = s (h0 + h1)/2, beta = s (h0 - h1)/2,
+// h0 = Hs[u,0], h1 = Hs[u,M/2]; the row pass stores alpha in the filter column
+// 0 and beta in a separate vector.
+#pragma once
+
+#include "fft_core.cuh"
+#include "layout.cuh"
+
+namespace gbfft {
+
+template <int N> struct ColCfg {
+    static constexpr int E = N < 16 ? N : 16;
+    static constexpr int T = N / E;
+    static constexpr int W = T >= 256 ? 1 : 256 / T;  // columns per block
+    static constexpr int THREADS = W * T;
+    static constexpr size_t SMEM = (size_t)W * padded_len(N) * sizeof(float2);
+};
+
+// slot of row u = t + T e (compile-time e, so the branch folds away)
+template <int N, int E, int T>
+__device__ __forceinline__ int slot_e(int t, int e, int log2g) {
+    int p, side;
+    if (e < E / 2) {
+        p = t + T * e;
+        side = 0;
+    } else {
+        p = (e == E / 2 && t == 0) ? 0 : N - (t + T * e);
+        side = 1;
+    }
+    return ((p >> log2g) << (log2g + 1)) + (side << log2g) + (p & ((1 << log2g) - 1));
+}
+
+// One block's share of the column pass: half-spectrum columns bx*W .. bx*W + W - 1
+// of one image.  spec: that image's half spectra [M/2][N] (slot order), hs /
+// beta: its prepared filter.
+template <int N>
+__device__ __forceinline__ void cols_body(float2 *spec, const float *__restrict__ hs, const float *__restrict__ beta,
+                                          int M, int log2g, const float2 *__restrict__ tw, int bx,
+                                          unsigned char *smraw) {
+    typedef ColCfg<N> K;
+    constexpr int E = K::E, T = K::T, W = K::W;
+    const int w = threadIdx.x / T;
+    const int t = threadIdx.x - w * T;
+    float2 *ex = reinterpret_cast<float2 *>(smraw) + w * padded_len(N);
+    const int half = M >> 1;
+    const int k0 = bx * W + w;
+    const bool active = k0 < half;  // narrow spectra: surplus column groups idle
+    const int k = active ? k0 : 0;
+    float2 *col = spec + (size_t)k * N;
+    const float *hcol = hs + (size_t)k * N;
+
+    float2 v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = active ? col[slot_e<N, E, T>(t, e, log2g)] : make_float2(0.f, 0.f);
+
+    fft_regs<N, E, -1>(v, ex, tw, t);
+
+    // the filter is read after the forward transform so it holds no registers during it
+    float h[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) h[e] = hcol[slot_e<N, E, T>(t, e, log2g)];
+
+    if (bx == 0) {  // the group of column 0 needs Q[-u] (uniform per block)
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < E; ++e) ex[pad16(t + T * e)] = v[e];
+        __syncthreads();
+    }
+    if (k != 0) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[e] = cscale(v[e], h[e]);
+    } else {
+        const float *bcol = beta;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int u = t + T * e;
+            const float2 qm = ex[pad16((N - u) & (N - 1))];
+            const float bt = bcol[slot_e<N, E, T>(t, e, log2g)];
+            v[e] = make_float2(h[e] * v[e].x + bt * qm.x, h[e] * v[e].y - bt * qm.y);
+        }
+    }
+
+    fft_regs<N, E, 1>(v, ex, tw, t);
+
+    if (active) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) col[slot_e<N, E, T>(t, e, log2g)] = v[e];
+    }
+}
+
+
+}  // namespace gbfft

@@ -38,21 +38,37 @@ cudaError_t launch_fourstep_a(const void *in, void *tmp, int log2n, long long ba
 cudaError_t launch_fourstep_b(const void *tmp, void *out, int log2n, long long batch, bool dbl, int dir,
                               const void *tw_n2, double scale, cudaStream_t s);
 
-// 2D pipeline stages (float32 images, complex64 half spectra [img][rows][cols/2],
-// column 0 of a half spectrum row packs (DC, Nyquist) as (re, im)).
-cudaError_t launch_rows_fwd(const float *img, void *spec, int rows, int cols, int nimg, const void *tw_cols,
-                            cudaStream_t s);
-// `variant` selects the column-tile width (0 = default; see cols.cu).
-cudaError_t launch_cols_filter(void *spec, const float *H, long long h_stride, int rows, int cols, int nimg,
-                               float scale, const void *tw_rows, cudaStream_t s, int variant = 0);
-int cols_variants();
-bool cols_variant_valid(int rows, int cols, int variant);
-// Adjoint column pass (cols_grad.cu): per column tile, loop over nimg images of
-// spec_x / spec_g, accumulate grad_H = scale * sum Re(conj(W G) W x) (added to
-// grad_H's contents when `accumulate`), and filter + inverse-transform spec_g.
-cudaError_t launch_cols_grad(const void *spec_x, void *spec_g, const float *H, float *grad_H, int rows, int cols,
-                             int nimg, float scale, int accumulate, const void *tw_rows, cudaStream_t s);
+// 2D pipeline stages (float32 images).  Intermediate, per image: half spectra
+// [cols/2][rows] complex64, column-major in slot order (layout.cuh; column 0
+// packs (DC, Nyquist) of each real row); prepared filter s * Hs [cols/2][rows]
+// float32 in the same order (column 0: alpha) and beta [rows].
+struct RowsFwdArgs {
+    const float *img;   // [nimg][rows][cols]
+    void *spec;         // [nimg][cols/2][rows] complex64
+    int rows, cols, nimg;
+    const float *H;     // filter of image 0 of this launch (row-major [rows][cols])
+    float *hs;          // prepared filter (one, or one per image when filter_mode == 2)
+    float *beta;
+    long long h_stride; // elements between consecutive images' filters (filter_mode 2)
+    int filter_mode;    // 0: none, 1: one shared filter (prepared by image 0), 2: per image
+    float scale;        // s = 1/(rows * cols)
+    const void *tw;     // twiddles of length cols
+};
+int rows_pairs_per_block(int cols);
+cudaError_t launch_rows_fwd(const RowsFwdArgs &a, cudaStream_t s);
+// hs_img / beta_img: elements between images' prepared filters (0 = shared)
+cudaError_t launch_cols_filter(void *spec, const float *hs, const float *beta, long long hs_img, long long beta_img,
+                               int rows, int cols, int nimg, const void *tw_rows, cudaStream_t s);
 cudaError_t launch_rows_inv(const void *spec, float *out, int rows, int cols, int nimg, const void *tw_cols,
                             cudaStream_t s);
+// Adjoint column pass (cols_grad.cu): per column, loop over nimg images of
+// spec_x / spec_g, accumulate scale * sum Re(conj(W G) W x) into grad_T
+// [cols/2 + 1][rows] (slot order; added to its contents when `accumulate`),
+// and filter + inverse-transform spec_g in place.  Shared filter only.
+cudaError_t launch_cols_grad(const void *spec_x, void *spec_g, const float *hs, const float *beta, float *grad_T,
+                             int rows, int cols, int nimg, float scale, int accumulate, const void *tw_rows,
+                             cudaStream_t s);
+// grad_T -> grad_H [rows][cols] row-major (both bins of every mirror pair).
+cudaError_t launch_grad_scatter(const float *grad_T, float *grad_H, int rows, int cols, cudaStream_t s);
 
 }  // namespace gbfft

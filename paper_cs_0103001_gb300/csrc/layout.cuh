@@ -1,0 +1,60 @@
+// layout.cuh — where the 2D pipeline keeps its half spectra and filter.
+//
+// The row pass transforms two image rows as one complex row.  It pairs each
+// row x with its mirror N - x (pair p: rows (p, N - p) for 0 < p < N/2, and
+// (0, N/2) for p = 0), because the symmetrised filter of frequency row u,
+// Hs[u][k] = (H[u][k] + H[-u][-k]) / 2, needs exactly filter rows u and -u:
+// the block that owns the pair reads both once, contiguously.
+//
+// Intermediate layout ("slot order", private to the library): for each
+// half-spectrum column k the N row values are contiguous (column-major), so
+// the column pass reads and writes whole columns.  Within a column, rows are
+// stored in the order the row pass produces them: groups of G pairs (G = the
+// row pass's pairs per block, capped at N/2), each group holding its G
+// "first" rows, then its G "mirror" rows:
+//   slot(x) = (p / G) * 2G + side * G + (p mod G),
+// with (p, side) the pair and side of row x.  A row-pass block therefore
+// writes 2G consecutive slots of every column (64 bytes of complex64 for
+// G = 4) and the inverse row pass reads them back the same way.
+#pragma once
+
+namespace gbfft {
+
+// pair index and side (0: first row, 1: mirror row) of row x of an N-row image
+__host__ __device__ __forceinline__ void pair_of(int x, int N, int &p, int &side) {
+    const int h = N >> 1;
+    if (x < h) {
+        p = x;
+        side = 0;
+    } else if (x == h) {
+        p = 0;
+        side = 1;
+    } else {
+        p = N - x;
+        side = 1;
+    }
+}
+
+// rows of pair p
+__host__ __device__ __forceinline__ void rows_of_pair(int p, int N, int &a, int &b) {
+    a = p;
+    b = p == 0 ? (N >> 1) : N - p;
+}
+
+// G is a power of two: log2g = log2(G)
+__host__ __device__ __forceinline__ int slot_of(int x, int N, int log2g) {
+    int p, side;
+    pair_of(x, N, p, side);
+    return ((p >> log2g) << (log2g + 1)) + (side << log2g) + (p & ((1 << log2g) - 1));
+}
+
+__host__ __device__ __forceinline__ int row_of_slot(int s, int N, int log2g) {
+    const int grp = s >> (log2g + 1);
+    const int side = (s >> log2g) & 1;
+    const int p = (grp << log2g) + (s & ((1 << log2g) - 1));
+    int a, b;
+    rows_of_pair(p, N, a, b);
+    return side ? b : a;
+}
+
+}  // namespace gbfft

@@ -1,0 +1,225 @@
+// rows_impl.cuh — the row passes of the Sec. 5 pipeline (fft2 -> filter -> ifft2).
+//
+// Sec. 4 computes a 2D transform as "FFT on rows, then FFT on columns".  The
+// image is real, so two image rows a, b are transformed together as one
+// complex row z = a + i b (length M); their spectra separate as
+//   A[k] = (Z[k] + conj Z[M-k]) / 2,   B[k] = (Z[k] - conj Z[M-k]) / (2i).
+// A real row has a Hermitian spectrum, so only bins 0..M/2 are kept; A[0] and
+// A[M/2] are real and share one complex slot (re = DC, im = Nyquist).  The
+// half spectra go to the workspace column-major in slot order (layout.cuh):
+// each block stages its rows' values in shared memory and writes 2G
+// consecutive slots of every column.
+//
+// The forward pass also prepares the filter for the column pass: for its
+// pair of mirror rows u = a, b it reads filter rows u and -u once and writes
+// s * Hs[u][k] (s = 1/(N M), Hs the even part of H) for k = 1..M/2-1 and, for
+// the packed column 0, alpha = s (h0 + h1) / 2 and beta = s (h0 - h1) / 2 with
+// h0 = Hs[u][0], h1 = Hs[u][M/2].
+//
+// The inverse pass reads its rows' slots back, rebuilds Z[k] = A[k] + i B[k]
+// for all k (A[M-k] = conj A[k]), runs one unscaled inverse FFT (Eq. E3) and
+// writes Re z to row a and Im z to row b.
+#pragma once
+
+#include "fft_core.cuh"
+#include "layout.cuh"
+
+namespace gbfft {
+
+template <int M> struct RowCfg {
+    static constexpr int E = M < 16 ? M : 16;
+    static constexpr int T = M / E;
+    // row pairs per block: 512 threads (two blocks per SM), at least 2 pairs
+    // (32-byte runs of complex64 per column)
+    static constexpr int PPC = (512 / T) > 2 ? 512 / T : 2;
+    static constexpr int THREADS = PPC * T;  // 512, or 1024 for M = 8192
+    static constexpr int SR = 2 * PPC + 1;                    // staging row stride (odd: no bank conflicts)
+    static constexpr int EXCH = PPC * padded_len(M);
+    static constexpr int STAGE = (M / 2) * SR;
+    static constexpr size_t SMEM = (size_t)(EXCH > STAGE ? EXCH : STAGE) * sizeof(float2);
+};
+
+// One block's share of the forward row pass: row pairs bx*G .. bx*G + G - 1 of
+// one image.  img: the image [N][M]; spec: its half spectra [M/2][N] (slot
+// order); with `prep`, also the prepared filter of frequency rows of those
+// pairs from H (row-major [N][M]) into hs [M/2][N] and beta [N].  Every thread
+// of the block must call it; it ends after a block-wide barrier-free epilogue,
+// so a caller that reuses shared memory must synchronise first.
+template <int M>
+__device__ __forceinline__ void rows_fwd_body(const float *__restrict__ img, float2 *__restrict__ spec,
+                                              const float *__restrict__ H, float *__restrict__ hs,
+                                              float *__restrict__ beta, int N, int log2g, bool prep, float scale,
+                                              const float2 *__restrict__ tw, int bx, unsigned char *smraw) {
+    typedef RowCfg<M> K;
+    constexpr int E = K::E, T = K::T, SR = K::SR, H2 = M / 2;
+    float2 *sm = reinterpret_cast<float2 *>(smraw);
+    const int G = 1 << log2g;
+    const int g = threadIdx.x / T;
+    const int t = threadIdx.x - g * T;
+    const int p = bx * G + g;
+    const bool active = g < G;  // the grid covers exactly N/2 pairs in groups of G
+    int a, b;
+    rows_of_pair(active ? p : 0, N, a, b);
+
+    float2 v[E];
+    if (active) {
+        const float *ra = img + (size_t)a * M;
+        const float *rb = img + (size_t)b * M;
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[e] = make_float2(__ldcs(ra + t + T * e), __ldcs(rb + t + T * e));
+    } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[e] = make_float2(0.f, 0.f);
+    }
+    float2 *ex = sm + g * padded_len(M);
+    fft_regs<M, E, -1>(v, ex, tw, t);
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < E; ++e) ex[pad16(t + T * e)] = v[e];
+    __syncthreads();
+    // split the two rows' spectra: ab[e] = A[k], ab[E/2 + e] = B[k], k = t + T e
+    float2 ab[E];
+#pragma unroll
+    for (int e = 0; e < E / 2; ++e) {
+        const int k = t + T * e;
+        const float2 zk = v[e];
+        if (e == 0 && t == 0) {
+            const float2 zn = v[E / 2];  // Z[M/2]
+            ab[e] = make_float2(zk.x, zn.x);
+            ab[E / 2 + e] = make_float2(zk.y, zn.y);
+        } else {
+            const float2 zm = ex[pad16(M - k)];
+            ab[e] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+            ab[E / 2 + e] = make_float2(0.5f * (zk.y + zm.y), 0.5f * (zm.x - zk.x));
+        }
+    }
+    __syncthreads();  // exchange buffers are reused as the staging area
+    float2 *stg = sm;
+    if (active) {
+#pragma unroll
+        for (int e = 0; e < E / 2; ++e) {
+            const int k = t + T * e;
+            stg[k * SR + g] = ab[e];
+            stg[k * SR + G + g] = ab[E / 2 + e];
+        }
+    }
+    __syncthreads();
+    {
+        // two slots (16 bytes) per thread; 2G >= 2 and every run starts 16-byte aligned
+        float2 *sb = spec + (size_t)bx * 2 * G;
+        const int n = H2 << log2g;
+        for (int idx = threadIdx.x; idx < n; idx += K::THREADS) {
+            const int k = idx >> log2g, s = (idx & (G - 1)) * 2;
+            const float2 x0 = stg[k * SR + s], x1 = stg[k * SR + s + 1];
+            *reinterpret_cast<float4 *>(sb + (size_t)k * N + s) = make_float4(x0.x, x0.y, x1.x, x1.y);
+        }
+    }
+    if (!prep) return;  // uniform per block
+
+    // ---- filter preparation for frequency rows a and b
+    const float *hb = H;
+    float *stf = reinterpret_cast<float *>(smraw);
+    __syncthreads();  // staging reads done
+    if (active) {
+        const int ma = (N - a) & (N - 1), mb = (N - b) & (N - 1);
+        const float *Ha = hb + (size_t)a * M, *Hma = hb + (size_t)ma * M;
+        const float *Hb = hb + (size_t)b * M, *Hmb = hb + (size_t)mb * M;
+#pragma unroll
+        for (int e = 0; e < E / 2; ++e) {
+            const int k = t + T * e;
+            if (e == 0 && t == 0) {
+                const float h0a = 0.5f * (Ha[0] + Hma[0]), h1a = 0.5f * (Ha[H2] + Hma[H2]);
+                const float h0b = 0.5f * (Hb[0] + Hmb[0]), h1b = 0.5f * (Hb[H2] + Hmb[H2]);
+                stf[g] = 0.5f * scale * (h0a + h1a);
+                stf[G + g] = 0.5f * scale * (h0b + h1b);
+                float *bb = beta + (size_t)bx * 2 * G;
+                bb[g] = 0.5f * scale * (h0a - h1a);
+                bb[G + g] = 0.5f * scale * (h0b - h1b);
+            } else {
+                const int km = M - k;
+                stf[k * SR + g] = 0.5f * scale * (Ha[k] + Hma[km]);
+                stf[k * SR + G + g] = 0.5f * scale * (Hb[k] + Hmb[km]);
+            }
+        }
+    }
+    __syncthreads();
+    float *hsb = hs + (size_t)bx * 2 * G;
+    const int n = H2 << (log2g + 1);
+    for (int idx = threadIdx.x; idx < n; idx += K::THREADS) {
+        const int k = idx >> (log2g + 1), s = idx & (2 * G - 1);
+        hsb[(size_t)k * N + s] = stf[k * SR + s];
+    }
+}
+
+// One block's share of the inverse row pass: spec [M/2][N] (slot order) of one
+// image -> rows of pairs bx*G .. bx*G + G - 1 of out [N][M], unscaled.
+template <int M>
+__device__ __forceinline__ void rows_inv_body(const float2 *__restrict__ spec, float *__restrict__ out, int N,
+                                              int log2g, const float2 *__restrict__ tw, int bx,
+                                              unsigned char *smraw) {
+    typedef RowCfg<M> K;
+    constexpr int E = K::E, T = K::T, SR = K::SR, H2 = M / 2;
+    float2 *sm = reinterpret_cast<float2 *>(smraw);
+    const int G = 1 << log2g;
+    const int g = threadIdx.x / T;
+    const int t = threadIdx.x - g * T;
+    const int p = bx * G + g;
+    const bool active = g < G;
+    int a, b;
+    rows_of_pair(active ? p : 0, N, a, b);
+
+    float2 *stg = sm;
+    {
+        const float2 *sb = spec + (size_t)bx * 2 * G;
+        const int n = H2 << log2g;
+        for (int idx = threadIdx.x; idx < n; idx += K::THREADS) {
+            const int k = idx >> log2g, s = (idx & (G - 1)) * 2;
+            const float4 x = *reinterpret_cast<const float4 *>(sb + (size_t)k * N + s);
+            stg[k * SR + s] = make_float2(x.x, x.y);
+            stg[k * SR + s + 1] = make_float2(x.z, x.w);
+        }
+    }
+    __syncthreads();
+    float2 v[E];
+    if (active) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int k = t + T * e;
+            float2 A, B;
+            if (e < E / 2) {  // 0 <= k < M/2
+                A = stg[k * SR + g];
+                B = stg[k * SR + G + g];
+                if (e == 0 && t == 0) {
+                    A.y = 0.f;
+                    B.y = 0.f;
+                }
+            } else if (e == E / 2 && t == 0) {  // k = M/2: the packed Nyquist bins
+                A = make_float2(stg[g].y, 0.f);
+                B = make_float2(stg[G + g].y, 0.f);
+            } else {  // M/2 < k < M: A[k] = conj A[M-k]
+                const int km = M - k;
+                const float2 am = stg[km * SR + g], bm = stg[km * SR + G + g];
+                A = make_float2(am.x, -am.y);
+                B = make_float2(bm.x, -bm.y);
+            }
+            v[e] = make_float2(A.x - B.y, A.y + B.x);  // A + i B
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[e] = make_float2(0.f, 0.f);
+    }
+    // the exchange buffers overlap the staging area: the first exchange of
+    // fft_regs starts with a block barrier, after every thread read its values
+    fft_regs<M, E, 1>(v, sm + g * padded_len(M), tw, t);
+    if (active) {
+        float *ra = out + (size_t)a * M;
+        float *rb = out + (size_t)b * M;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            __stcs(ra + t + T * e, v[e].x);
+            __stcs(rb + t + T * e, v[e].y);
+        }
+    }
+}
+
+}  // namespace gbfft
