@@ -40,8 +40,12 @@ WORKLOAD = "fft2_butterworth_ifft2_4096x4096_fp32"
 METRIC = "2D FFT→filter→IFFT GB/s & % HBM peak at 4096² fp32, rel-L2 vs FP64 oracle"
 COMPULSORY_BYTES_PER_PX = 12  # img 4 + H 4 + out 4
 NOMINAL_C2C_BYTES_PER_PX = 44  # three-pass complex-to-complex schedule
-# algorithmic bytes per pixel of each stage of the half-spectrum schedule
-STAGE_BYTES_PER_PX = {"rows_fwd": 8, "cols_filter": 12, "rows_inv": 8}
+# algorithmic bytes per pixel of each stage of the half-spectrum schedule:
+# forward rows read img (4) and write half spectra (4); the filter preparation
+# reads H (4) and writes the even part on the half spectrum (2); the column
+# pass reads spectra (4) and prepared filter (2) and writes spectra (4); the
+# inverse rows read spectra (4) and write out (4)
+STAGE_BYTES_PER_PX = {"rows_fwd": 8, "filter_prep": 6, "cols_filter": 10, "rows_inv": 8}
 FLOPS_PER_IMAGE = 2 * 5 * ROWS * COLS * math.log2(ROWS * COLS) + 2 * ROWS * COLS
 
 

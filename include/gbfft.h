@@ -115,7 +115,8 @@ typedef enum {
     GBFFT_STAGE_COLS_GRAD = 6, /* 2D fused column pass of the adjoint (grad_H) */
     GBFFT_STAGE_TWIDDLES = 7,  /* twiddle-table generation (bind time) */
     GBFFT_STAGE_GRAPH = 8,     /* one replay of a batched plan's captured graph */
-    GBFFT_STAGE_COUNT = 9
+    GBFFT_STAGE_FILTER_PREP = 9, /* 2D: even part of the filter, slot order (side stream) */
+    GBFFT_STAGE_COUNT = 10
 } gbfft_stage;
 
 /* ---- plans --------------------------------------------------------------- */
@@ -159,7 +160,9 @@ int fft_inverse(gbfft_plan_t plan, const void *in, void *out, gbfft_stream_t str
  * real filter in natural (unshifted) DFT order; image b uses
  * H + b * h_batch_stride (option GBFFT_OPT_H_BATCH_STRIDE, default 0).
  * The filter multiplies the real and the imaginary part of every spectral
- * value.  img == out is allowed. */
+ * value.  img == out is allowed.  The filter preparation runs on a side
+ * stream of the plan, forked from and joined back to `stream` with events,
+ * so the call stays ordered on `stream` (and can be captured in a graph). */
 int fft2_filter_ifft2(gbfft_plan_t plan, const float *img, const float *H, float *out, gbfft_stream_t stream);
 
 /* Adjoint of fft2_filter_ifft2 for an upstream gradient grad_out = dL/dout

@@ -12,6 +12,16 @@ Importing this package loads libgbfft.so and fails if it is missing; build it
 with ``paper_cs_0103001_gb300.build.build()``.
 """
 
-from .api import Plan1D, Plan2D, clear_plan_cache, fft, fft2_filter_ifft2, ifft  # noqa: F401
+from .api import (  # noqa: F401
+    Plan1D,
+    Plan2D,
+    Plan2DBatched,
+    clear_plan_cache,
+    fft,
+    fft2_filter_ifft2,
+    fft2_filter_ifft2_batched,
+    ifft,
+)
 
-__all__ = ["fft", "ifft", "fft2_filter_ifft2", "Plan1D", "Plan2D", "clear_plan_cache"]
+__all__ = ["fft", "ifft", "fft2_filter_ifft2", "fft2_filter_ifft2_batched", "Plan1D", "Plan2D", "Plan2DBatched",
+           "clear_plan_cache"]

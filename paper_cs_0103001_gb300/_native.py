@@ -41,7 +41,7 @@ OPT_USE_GRAPH = 8
 
 # gbfft_stage
 STAGES = ("fft1d", "fourstep_a", "fourstep_b", "rows_fwd", "cols_filter", "rows_inv", "cols_grad", "twiddles",
-          "graph")
+          "graph", "filter_prep")
 
 # every exported symbol with (restype, argtypes)
 _P = ctypes.c_void_p

@@ -124,6 +124,57 @@ class Plan2D(_PlanBase):
         return grad_img, grad_H
 
 
+class Plan2DBatched(_PlanBase):
+    """Sec. 5 pipeline over images of uneven power-of-two sizes (16..4096 per
+    side), each with its own filter, in three persistent launches (optionally
+    replayed from a CUDA graph).  `shapes` is a list of (rows, cols)."""
+
+    def __init__(self, shapes, device, options=None):
+        n = len(shapes)
+        rows = (ctypes.c_int64 * n)(*[int(r) for r, _ in shapes])
+        cols = (ctypes.c_int64 * n)(*[int(c) for _, c in shapes])
+        h = _P()
+        nat.call("fft2_batched_plan_create", n, rows, cols, ctypes.byref(h))
+        self.shapes = [(int(r), int(c)) for r, c in shapes]
+        super().__init__(h, torch.device(device), options)
+        # device array of gbfft_image_ptrs {img, H, out}; its address stays fixed
+        # so a captured graph keeps reading the current pointers
+        self.ptrs = torch.zeros(n, 3, dtype=torch.int64, device=self.device)
+
+    def _set_pointers(self, imgs, Hs, outs):
+        if not (len(imgs) == len(Hs) == len(outs) == len(self.shapes)):
+            raise ValueError("one image, filter and output per planned shape")
+        table = []
+        for (r, c), a, h, o in zip(self.shapes, imgs, Hs, outs):
+            for t in (a, h, o):
+                if t.dtype != torch.float32 or tuple(t.shape[-2:]) != (r, c) or not t.is_contiguous() or not t.is_cuda:
+                    raise ValueError(f"expected contiguous float32 CUDA tensors of shape ({r}, {c})")
+            table.append([a.data_ptr(), h.data_ptr(), o.data_ptr()])
+        self.ptrs.copy_(torch.tensor(table, dtype=torch.int64), non_blocking=False)
+
+    def filter(self, imgs, Hs, outs=None):
+        if outs is None:
+            outs = [torch.empty_like(a) for a in imgs]
+        with self.lock:
+            self._set_pointers(imgs, Hs, outs)
+            nat.call("fft2_filter_ifft2_batched", self.handle, _ptr(self.ptrs), _stream_handle(self.device))
+        return outs
+
+    def autotune(self, imgs, Hs, outs=None):
+        """Time the launch shapes on these inputs and keep the fastest."""
+        if outs is None:
+            outs = [torch.empty_like(a) for a in imgs]
+        with self.lock:
+            self._set_pointers(imgs, Hs, outs)
+            nat.call("fft_plan_autotune", self.handle, _ptr(self.ptrs), _stream_handle(self.device))
+        return self.get_option(nat.OPT_BLOCKS_PER_SM)
+
+    def get_option(self, key: int) -> int:
+        v = ctypes.c_int64()
+        nat.call("fft_plan_get_option", self.handle, int(key), ctypes.byref(v))
+        return int(v.value)
+
+
 _cache: dict[tuple, _PlanBase] = {}
 _cache_lock = threading.Lock()
 
@@ -212,6 +263,20 @@ class _FilterFn(torch.autograd.Function):
         grad_H = torch.empty_like(H) if need_H else None
         plan.backward(img, H, g, grad_img, grad_H)
         return grad_img, grad_H
+
+
+def fft2_filter_ifft2_batched(imgs, Hs):
+    """Sec. 5 pipeline over a list of float32 images of (possibly) different
+    power-of-two shapes, each with its own filter; returns a list of outputs.
+    Not differentiable; the plan is cached per list of shapes and device."""
+    if len(imgs) != len(Hs) or not imgs:
+        raise ValueError("need one filter per image")
+    for a, h in zip(imgs, Hs):
+        _check_2d(a, h)
+    dev = imgs[0].device
+    shapes = tuple((int(a.shape[-2]), int(a.shape[-1])) for a in imgs)
+    plan = _cached(("batched", shapes, dev), lambda: Plan2DBatched(shapes, dev))
+    return plan.filter([a.contiguous() for a in imgs], [h.contiguous() for h in Hs])
 
 
 def fft2_filter_ifft2(img: torch.Tensor, H: torch.Tensor) -> torch.Tensor:

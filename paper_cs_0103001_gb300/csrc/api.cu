@@ -68,6 +68,10 @@ struct gbfft_plan {
     cudaGraphExec_t graph_exec = nullptr;
     const void *graph_ptrs = nullptr;
     int graph_grid[3] = {0, 0, 0};
+    // 2D: side stream for the filter preparation, forked from / joined to the
+    // caller's stream with events
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace {
@@ -452,8 +456,17 @@ int fft_inverse(gbfft_plan_t p, const void *in, void *out, gbfft_stream_t stream
     return run_1d(p, in, out, +1, reinterpret_cast<cudaStream_t>(stream));
 }
 
-// One chunk of the Sec. 5 pipeline: row pass (+ filter preparation), fused
-// column pass, inverse row pass.
+static cudaError_t ensure_aux(gbfft_plan *p) {
+    cudaError_t e = cudaSuccess;
+    if (!p->aux) e = cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !p->ev_fork) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess && !p->ev_join) e = cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming);
+    return e;
+}
+
+// One chunk of the Sec. 5 pipeline: filter preparation on the side stream
+// while the forward row pass runs, then the fused column pass and the inverse
+// row pass.
 static int pipeline_chunk(gbfft_plan *p, const float *img, const float *H, float *out, int nb, bool first,
                           cudaStream_t s) {
     const int rows = 1 << p->log2r, cols = 1 << p->log2c;
@@ -469,11 +482,29 @@ static int pipeline_chunk(gbfft_plan *p, const float *img, const float *H, float
     a.hs = reinterpret_cast<float *>(p->ws + p->off_hs);
     a.beta = reinterpret_cast<float *>(p->ws + p->off_beta);
     a.h_stride = p->opt_h_stride;
-    a.filter_mode = per_image ? 2 : (first ? 1 : 0);  // a shared filter is prepared once per call
+    a.filter_mode = 0;  // prepared separately below
     a.scale = (float)(1.0 / ((double)rows * cols));
     a.tw = p->ws + p->off_tw0;
-    int rc = launch(p, GBFFT_STAGE_ROWS_FWD, s, [&] { return launch_rows_fwd(a, s); });
+    const bool prep = per_image || first;  // a shared filter is prepared once per call
+    int rc;
+    if (prep) {
+        cudaError_t e = ensure_aux(p);
+        if (e == cudaSuccess) e = cudaEventRecord(p->ev_fork, s);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(p->aux, p->ev_fork, 0);
+        if (e != cudaSuccess) return cuda_fail(e);
+        rc = launch(p, GBFFT_STAGE_FILTER_PREP, p->aux, [&] {
+            return launch_filter_prep(H, a.hs, a.beta, rows, cols, per_image ? nb : 1, a.scale, p->opt_h_stride,
+                                      per_image ? half_px : 0, per_image ? rows : 0, p->aux);
+        });
+        if (rc) return rc;
+        if ((e = cudaEventRecord(p->ev_join, p->aux)) != cudaSuccess) return cuda_fail(e);
+    }
+    rc = launch(p, GBFFT_STAGE_ROWS_FWD, s, [&] { return launch_rows_fwd(a, s); });
     if (rc) return rc;
+    if (prep) {
+        cudaError_t e = cudaStreamWaitEvent(s, p->ev_join, 0);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
     rc = launch(p, GBFFT_STAGE_COLS, s, [&] {
         return launch_cols_filter(a.spec, a.hs, a.beta, per_image ? half_px : 0, per_image ? rows : 0, rows, cols, nb,
                                   p->ws + p->off_tw1, s);
@@ -745,6 +776,9 @@ int fft_plan_destroy(gbfft_plan_t p) {
     if (!p) return GBFFT_ERR_NULL;
     drop_graph(p);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+    if (p->aux) cudaStreamDestroy(p->aux);
+    if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+    if (p->ev_join) cudaEventDestroy(p->ev_join);
     for (auto &r : p->prof) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);

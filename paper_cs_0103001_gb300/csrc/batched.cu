@@ -17,8 +17,10 @@
 
 namespace gbfft {
 
+// The per-size bodies are kept out of line: each gets its own register
+// allocation instead of the union of all sizes inlined into one loop.
 template <int L>
-__device__ __forceinline__ void fwd_case(const BatchImage &im, const gbfft_image_ptrs &pp, char *ws, int bx,
+__device__ __noinline__ void fwd_case(const BatchImage &im, const gbfft_image_ptrs &pp, char *ws, int bx,
                                          unsigned char *sm) {
     rows_fwd_body<(1 << L)>(pp.img, reinterpret_cast<float2 *>(ws + im.spec_off), pp.H,
                             reinterpret_cast<float *>(ws + im.hs_off), reinterpret_cast<float *>(ws + im.beta_off),
@@ -27,14 +29,14 @@ __device__ __forceinline__ void fwd_case(const BatchImage &im, const gbfft_image
 }
 
 template <int L>
-__device__ __forceinline__ void inv_case(const BatchImage &im, const gbfft_image_ptrs &pp, char *ws, int bx,
+__device__ __noinline__ void inv_case(const BatchImage &im, const gbfft_image_ptrs &pp, char *ws, int bx,
                                          unsigned char *sm) {
     rows_inv_body<(1 << L)>(reinterpret_cast<const float2 *>(ws + im.spec_off), pp.out, im.rows, im.log2g,
                             reinterpret_cast<const float2 *>(ws + im.twc_off), bx, sm);
 }
 
 template <int L>
-__device__ __forceinline__ void cols_case(const BatchImage &im, char *ws, int bx, unsigned char *sm) {
+__device__ __noinline__ void cols_case(const BatchImage &im, char *ws, int bx, unsigned char *sm) {
     cols_body<(1 << L)>(reinterpret_cast<float2 *>(ws + im.spec_off), reinterpret_cast<const float *>(ws + im.hs_off),
                         reinterpret_cast<const float *>(ws + im.beta_off), im.cols, im.log2g,
                         reinterpret_cast<const float2 *>(ws + im.twr_off), bx, sm);
@@ -149,7 +151,7 @@ cudaError_t batch_max_blocks_per_sm(int stage, size_t smem, int *blocks) {
                     : stage == 1 ? (const void *)k_batched_cols
                                  : (const void *)k_batched_rows_inv;
     const int threads = stage == 1 ? kBatchColThreads : kBatchRowThreads;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = set_smem_attrs(k, smem, 2);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, k, threads, smem);
 }

@@ -19,10 +19,8 @@ static cudaError_t run_cols(void *spec, const float *hs, const float *beta, long
                             int cols, int nimg, int log2g, const void *tw, cudaStream_t s) {
     typedef ColCfg<N> K;
     auto kern = k_cols_filter<N>;
-    if (K::SMEM > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::SMEM);
-        if (e != cudaSuccess) return e;
-    }
+    cudaError_t e = set_smem_attrs((const void *)kern, K::SMEM, 2);
+    if (e != cudaSuccess) return e;
     const int half = cols / 2;
     dim3 grid((half + K::W - 1) / K::W, nimg);
     kern<<<grid, K::THREADS, K::SMEM, s>>>(static_cast<float2 *>(spec), hs, beta, hs_img, beta_img, cols, log2g,

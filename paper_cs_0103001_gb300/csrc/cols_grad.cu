@@ -171,10 +171,8 @@ static cudaError_t run_grad(const void *spec_x, void *spec_g, const float *hs, c
                             cudaStream_t s) {
     typedef GradCfg<N> K;
     auto kern = k_cols_grad<N>;
-    if (K::SMEM > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::SMEM);
-        if (e != cudaSuccess) return e;
-    }
+    cudaError_t e = set_smem_attrs((const void *)kern, K::SMEM);
+    if (e != cudaSuccess) return e;
     const int half = cols / 2;
     dim3 grid((half + K::W - 1) / K::W);
     kern<<<grid, K::THREADS, K::SMEM, s>>>(static_cast<const float2 *>(spec_x), static_cast<float2 *>(spec_g), hs,

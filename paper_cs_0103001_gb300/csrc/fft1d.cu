@@ -57,10 +57,8 @@ static cudaError_t run_fft1d(const void *in, void *out, long long batch, int dir
     const long long grid = (batch + K::BPC - 1) / K::BPC;
     if (grid > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
     auto kern = dir < 0 ? k_fft1d<N, -1, R> : k_fft1d<N, 1, R>;
-    if (K::SMEM > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)K::SMEM);
-        if (e != cudaSuccess) return e;
-    }
+    cudaError_t e = set_smem_attrs((const void *)kern, K::SMEM);
+    if (e != cudaSuccess) return e;
     kern<<<(unsigned)grid, K::THREADS, K::SMEM, s>>>(static_cast<const C *>(in), static_cast<C *>(out), batch,
                                                       static_cast<const C *>(tw), (R)scale);
     return cudaGetLastError();

@@ -186,6 +186,23 @@ template <int R, int DIR, typename C> __device__ __forceinline__ void dft(C *a) 
 
 template <typename C> __device__ __forceinline__ C ldg_c(const C *p) { return __ldg(p); }
 
+// ------------------------------------------------------ host helpers ------
+// Allow `smem` bytes of dynamic shared memory per block and, when `blocks` >
+// 0, ask for a shared memory carve-out just large enough for that many blocks
+// per SM; the rest of the SM's 256 KB stays L1 cache (twiddle tables are read
+// through L1).  blocks = 0 leaves the carve-out to the driver.
+inline cudaError_t set_smem_attrs(const void *kern, size_t smem, int blocks = 0) {
+    cudaError_t e = cudaSuccess;
+    if (smem > 48 * 1024) e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (blocks <= 0 || e != cudaSuccess) return e;
+    const size_t need = (smem + 1024) * (size_t)blocks;  // 1 KB per block is reserved by the system
+    const size_t max_sm = 228 * 1024;
+    int pct = (int)((need * 100 + max_sm - 1) / max_sm);
+    if (pct > 100) pct = 100;
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, pct);
+    return e;
+}
+
 // ----------------------------------------------- asynchronous copies ------
 // cp.async (global -> shared without a register round trip); `bytes` is 4, 8
 // or 16 and both addresses must be aligned to it.

@@ -56,6 +56,10 @@ struct RowsFwdArgs {
 };
 int rows_pairs_per_block(int cols);
 cudaError_t launch_rows_fwd(const RowsFwdArgs &a, cudaStream_t s);
+// Prepared filter alone (same values as RowsFwdArgs filter_mode 1/2) for nimg
+// filters H + i * h_stride into hs + i * hs_img, beta + i * beta_img.
+cudaError_t launch_filter_prep(const float *H, float *hs, float *beta, int rows, int cols, int nimg, float scale,
+                               long long h_stride, long long hs_img, long long beta_img, cudaStream_t s);
 // hs_img / beta_img: elements between images' prepared filters (0 = shared)
 cudaError_t launch_cols_filter(void *spec, const float *hs, const float *beta, long long hs_img, long long beta_img,
                                int rows, int cols, int nimg, const void *tw_rows, cudaStream_t s);

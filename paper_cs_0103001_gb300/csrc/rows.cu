@@ -20,7 +20,7 @@ int rows_pairs_per_block(int cols) {
 // filter_mode 1: image 0's blocks also prepare the shared filter from H;
 // filter_mode 2: every image prepares its own from H + y * h_stride.
 template <int M>
-__global__ void __launch_bounds__(RowCfg<M>::THREADS)
+__global__ void __launch_bounds__(RowCfg<M>::THREADS, RowCfg<M>::THREADS <= 512 ? 2 : 1)
     k_rows_fwd(const float *__restrict__ img, float2 *__restrict__ spec, const float *__restrict__ H,
                float *__restrict__ hs, float *__restrict__ beta, int N, int log2g, long long h_stride,
                int filter_mode, float scale, const float2 *__restrict__ tw) {
@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(RowCfg<M>::THREADS)
 }
 
 template <int M>
-__global__ void __launch_bounds__(RowCfg<M>::THREADS)
+__global__ void __launch_bounds__(RowCfg<M>::THREADS, RowCfg<M>::THREADS <= 512 ? 2 : 1)
     k_rows_inv(const float2 *__restrict__ spec, float *__restrict__ out, int N, int log2g,
                const float2 *__restrict__ tw) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -41,10 +41,71 @@ __global__ void __launch_bounds__(RowCfg<M>::THREADS)
     rows_inv_body<M>(spec + y * (M / 2) * N, out + y * N * M, N, log2g, tw, blockIdx.x, smraw);
 }
 
+// Filter preparation on its own (the same values rows_fwd_body writes with
+// `prep`), as a tiled transpose: block (bx, by) of image z covers P mirror-row
+// pairs (a whole number of slot groups of G pairs) and K half-spectrum
+// columns.  It reads filter rows u and -u in runs of K floats (the mirror run
+// reversed), forms s * Hs[u][k] (column 0: alpha, plus beta), and writes each
+// column's 2P slots as one contiguous run.  It touches no spectrum, so it runs
+// concurrently with the forward row pass.
+__global__ void __launch_bounds__(256)
+    k_filter_prep(const float *__restrict__ H, float *__restrict__ hs, float *__restrict__ beta, int N, int M,
+                  int log2g, int log2p, int log2k, float scale, long long h_stride, long long hs_img,
+                  long long beta_img) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float *tile = reinterpret_cast<float *>(smraw);
+    const int G = 1 << log2g, P = 1 << log2p, K = 1 << log2k, H2 = M >> 1, SR = 2 * P + 1;
+    const int p0 = blockIdx.x * P, k0 = blockIdx.y * K;
+    const size_t z = blockIdx.z;
+    const float *hb = H + z * h_stride;
+    // rows of the tile: r = side * P + g, pair p0 + g; local slot of that row
+    const int n = (2 * P) << log2k;
+    for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+        const int r = idx >> log2k, i = idx & (K - 1);
+        const int side = r >> log2p, g = r & (P - 1);
+        int a, b;
+        rows_of_pair(p0 + g, N, a, b);
+        const int u = side ? b : a, mu = (N - u) & (N - 1);
+        const int ls = ((g >> log2g) << (log2g + 1)) + (side << log2g) + (g & (G - 1));
+        const int k = k0 + i;
+        const float *Hu = hb + (size_t)u * M, *Hm = hb + (size_t)mu * M;
+        float v;
+        if (k == 0) {
+            const float h0 = 0.5f * (Hu[0] + Hm[0]), h1 = 0.5f * (Hu[H2] + Hm[H2]);
+            v = 0.5f * scale * (h0 + h1);
+            beta[z * beta_img + 2 * (size_t)p0 + ls] = 0.5f * scale * (h0 - h1);
+        } else {
+            v = 0.5f * scale * (__ldcs(Hu + k) + __ldcs(Hm + (M - k)));
+        }
+        tile[i * SR + ls] = v;
+    }
+    __syncthreads();
+    float *hsb = hs + z * hs_img + 2 * (size_t)p0;
+    const int m = K << (log2p + 1);
+    for (int idx = threadIdx.x; idx < m; idx += blockDim.x) {
+        const int i = idx >> (log2p + 1), s = idx & (2 * P - 1);
+        hsb[(size_t)(k0 + i) * N + s] = tile[i * SR + s];
+    }
+}
+
+cudaError_t launch_filter_prep(const float *H, float *hs, float *beta, int rows, int cols, int nimg, float scale,
+                               long long h_stride, long long hs_img, long long beta_img, cudaStream_t s) {
+    int g = rows_pairs_per_block(cols);
+    if (g > rows / 2) g = rows / 2;
+    int pp = g > 16 ? g : 16;  // pairs per tile: whole slot groups, runs of >= 32 slots
+    if (pp > rows / 2) pp = rows / 2;
+    int kk = cols / 2 < 32 ? cols / 2 : 32;
+    const size_t smem = (size_t)kk * (2 * pp + 1) * sizeof(float);
+    cudaError_t e = set_smem_attrs((const void *)k_filter_prep, smem);
+    if (e != cudaSuccess) return e;
+    dim3 grid((rows / 2) / pp, (cols / 2) / kk, nimg);
+    k_filter_prep<<<grid, 256, smem, s>>>(H, hs, beta, rows, cols, ilog2(g), ilog2(pp), ilog2(kk), scale, h_stride,
+                                          hs_img, beta_img);
+    return cudaGetLastError();
+}
+
 template <int M> static cudaError_t set_smem(const void *kern) {
-    if (RowCfg<M>::SMEM > 48 * 1024)
-        return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RowCfg<M>::SMEM);
-    return cudaSuccess;
+    return set_smem_attrs(kern, RowCfg<M>::SMEM, RowCfg<M>::THREADS <= 512 ? 2 : 1);
 }
 
 static int log2_pairs_per_block(int rows, int cols) {
