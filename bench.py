@@ -329,6 +329,8 @@ def run_gbfft(args):
             "rel_l2_tol": tol,
             "rel_l2_pass": rel <= tol,
             "stage_us": {k: round(1e3 * v[0] / v[1], 2) for k, v in stages.items()},
+            "stage_gbs": {k: round(STAGE_BYTES_PER_PX.get(k, 0) * px / (v[0] / v[1] * 1e-3) / 1e9, 1)
+                          for k, v in stages.items()},
             "roofline": {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 1), "peak": peak,
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
                          "traffic": traffic, "algorithmic_bytes": dom_bytes},
@@ -342,6 +344,7 @@ def run_gbfft(args):
                     "note": "pinned host image in, filtered image out, every step; filter resident; "
                             "copies overlapped with compute on three streams"},
             "gpu_launches": int(round(launches_per_step * args.steps)),
+            "variants": run_variants() if args.variants else None,
             "clocks": clk,
             "wall_s_timed": round(wall, 4),
         }
@@ -349,6 +352,147 @@ def run_gbfft(args):
         dist.barrier()
         dist.destroy_process_group()
     return result
+
+
+# --------------------------------------------------------------------------
+# Other workloads of the method (reported as "variants" on the headline line,
+# or alone with --workload for profiling).
+# --------------------------------------------------------------------------
+
+def _timed(fn, steps, warm, flush=None):
+    import torch
+
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    ms = []
+    for i in range(steps):
+        if flush is not None:
+            flush.fill_(i & 0xFF)
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        b.synchronize()
+        ms.append(a.elapsed_time(b))
+    return statistics.median(ms)
+
+
+def variant_fft1d(log2n: int, dtype: str = "c64", steps: int = 10):
+    """Batched 1D transforms (Eq. E2 forward), batch x N = 2^26 complex64
+    (complex128: N = 2^20, batch 64); GB/s of one read + one write."""
+    import torch
+
+    import paper_cs_0103001_gb300 as gb
+    from paper_cs_0103001_gb300 import synth
+
+    n = 1 << log2n
+    if dtype == "c64":
+        batch, tdt = (1 << 26) // n, torch.complex64
+    else:
+        batch, tdt = 64, torch.complex128
+    x = torch.from_numpy(synth.complex_uniform((batch, n), 2, log2n)).cuda().to(tdt)
+    y = torch.empty_like(x)
+    plan = gb.Plan1D(n, batch, tdt, "cuda")
+    ms = _timed(lambda: plan.forward(x, out=y), steps, 3)
+    nbytes = 2 * x.numel() * x.element_size()
+    return {"n": n, "batch": batch, "dtype": dtype, "us": round(ms * 1e3, 1),
+            "gbs_one_pass": round(nbytes / (ms * 1e-3) / 1e9, 1),
+            "gflops_5nlogn": round(5 * n * log2n * batch / (ms * 1e-3) / 1e9, 1)}
+
+
+def variant_batched(count: int = 512, steps: int = 5):
+    """Uneven batch: `count` skies, sides in {64..2048}, own Gaussian filter
+    each, three persistent launches replayed from a CUDA graph."""
+    import torch
+
+    import paper_cs_0103001_gb300 as gb
+    from paper_cs_0103001_gb300 import synth
+
+    batch = synth.uneven_batch(count, 4)
+    ti = [torch.from_numpy(a).cuda() for a, _, _ in batch]
+    th = [torch.from_numpy(h).cuda() for _, h, _ in batch]
+    to = [torch.empty_like(a) for a in ti]
+    plan = gb.Plan2DBatched([tuple(a.shape) for a in ti], "cuda")
+    plan.autotune(ti, th, to)
+    ms = _timed(lambda: plan.filter(ti, th, to), steps, 2)
+    px = sum(a.numel() for a in ti)
+    return {"images": count, "pixels": px, "ms": round(ms, 3), "images_per_s": round(count / (ms * 1e-3), 1),
+            "gbs_compulsory_12Bpx": round(12 * px / (ms * 1e-3) / 1e9, 1)}
+
+
+def variant_pipeline256(steps: int = 200):
+    """One 256 x 256 sky (50 sources), Gaussian low-pass sigma 32 bins:
+    latency of one call (inputs in L2; median)."""
+    import torch
+
+    import paper_cs_0103001_gb300 as gb
+    from paper_cs_0103001_gb300 import synth
+
+    img = torch.from_numpy(synth.sky(256, 256, 50, 1)).cuda()
+    H = torch.from_numpy(synth.gaussian_lowpass(256, 256, 32.0)).cuda()
+    out = torch.empty_like(img)
+    plan = gb.Plan2D(256, 256, 1, "cuda")
+    ms = _timed(lambda: plan.filter(img, H, out=out), steps, 20)
+    return {"us": round(ms * 1e3, 2)}
+
+
+def variant_backward(steps: int = 5):
+    """16 x 2048^2 noisy skies, learnable filter (init 1): forward and adjoint."""
+    import torch
+
+    import paper_cs_0103001_gb300 as gb
+    from paper_cs_0103001_gb300 import _native as nat
+    from paper_cs_0103001_gb300 import synth
+
+    x = torch.from_numpy(np.stack([synth.sky(2048, 2048, 5000, 5, b) for b in range(16)])).cuda()
+    H = torch.ones(2048, 2048, device="cuda")
+    g = torch.randn_like(x)
+    plan = gb.Plan2D(2048, 2048, 16, "cuda", {nat.OPT_ENABLE_BACKWARD: 1})
+    gi, gh, out = torch.empty_like(x), torch.empty_like(H), torch.empty_like(x)
+    fwd = _timed(lambda: plan.filter(x, H, out=out), steps, 2)
+    bwd = _timed(lambda: plan.backward(x, H, g, gi, gh), steps, 2)
+    return {"fwd_ms": round(fwd, 3), "bwd_ms": round(bwd, 3), "bwd_over_fwd": round(bwd / fwd, 2)}
+
+
+def run_variants():
+    import torch
+
+    out = {}
+    for name, fn in (("fft1d_c64_2^8", lambda: variant_fft1d(8)), ("fft1d_c64_2^12", lambda: variant_fft1d(12)),
+                     ("fft1d_c64_2^16", lambda: variant_fft1d(16)), ("fft1d_c64_2^20", lambda: variant_fft1d(20)),
+                     ("fft1d_c64_2^24", lambda: variant_fft1d(24)),
+                     ("fft1d_c128_2^20x64", lambda: variant_fft1d(20, "c128", 3)),
+                     ("pipeline_256", variant_pipeline256), ("backward_16x2048", variant_backward),
+                     ("batched_uneven_512", variant_batched)):
+        try:
+            out[name] = fn()
+        except Exception as e:  # report, do not hide the headline
+            out[name] = {"error": f"{type(e).__name__}: {e}"}
+        torch.cuda.empty_cache()
+    return out
+
+
+def run_workload(args):
+    """--workload other than the headline: one JSON line for that workload."""
+    import __graft_entry__
+
+    __graft_entry__._build_module().build()
+    import torch
+
+    torch.cuda.set_device(0)
+    if args.workload == "fft1d":
+        res = variant_fft1d(args.log2n, args.dtype, args.steps)
+    elif args.workload == "batched":
+        res = variant_batched(steps=args.steps)
+    elif args.workload == "pipeline256":
+        res = variant_pipeline256(args.steps)
+    elif args.workload == "backward2048":
+        res = variant_backward(args.steps)
+    else:
+        raise SystemExit(f"unknown workload {args.workload}")
+    return {"workload": args.workload, **res}
 
 
 def run_reference(args):
@@ -384,7 +528,16 @@ def main():
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gbfft", choices=["gbfft", "reference"])
+    ap.add_argument("--workload", default="pipeline4096",
+                    choices=["pipeline4096", "fft1d", "batched", "pipeline256", "backward2048"])
+    ap.add_argument("--log2n", type=int, default=20)
+    ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
+    ap.add_argument("--no-variants", dest="variants", action="store_false",
+                    help="headline only, without the other workloads")
     args = ap.parse_args()
+    if args.impl == "gbfft" and args.workload != "pipeline4096":
+        print(json.dumps(run_workload(args)), flush=True)
+        return
     if args.warmup < 3 and args.impl == "gbfft":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

@@ -81,14 +81,20 @@ typedef enum {
      * 0 (default) shares one H; rows*cols gives each image its own.  Changes
      * fft_plan_workspace_bytes (one prepared filter per image in a chunk). */
     GBFFT_OPT_H_BATCH_STRIDE = 2,
-    /* Arithmetic of the butterflies: 0 = FP32 (default for C64),
-     * 1 = split-BF16 tensor-core radix-16 stages (C64 only). */
+    /* Arithmetic of the 2D pipeline's radix-16 passes: 0 = FP32 butterflies
+     * (default); 1 = tensor cores, each operand split into 2 BF16 parts, 3
+     * products (about 16 significant bits per pass); 2 = 3 BF16 parts, 6
+     * products (about 24 bits).  Nonzero values need a 2D plan with sides
+     * 512..4096 (else GBFFT_ERR_UNSUPPORTED); the filter gradient of the
+     * adjoint is always computed with FP32 butterflies. */
     GBFFT_OPT_PRECISION = 3,
     /* 2D: number of images whose spectra share the workspace at a time
      * (0 = choose from the L2 size).  Changes fft_plan_workspace_bytes. */
     GBFFT_OPT_IMAGES_PER_CHUNK = 4,
     /* 1 = record a CUDA event pair around every kernel launch of this plan
-     * (read with gbfft_plan_profile_read); 0 (default) = off. */
+     * (read with gbfft_plan_profile_read) and run every kernel on the
+     * caller's stream, one after the other, so each pair times one kernel;
+     * 0 (default) = off. */
     GBFFT_OPT_PROFILE = 5,
     /* 2D: 1 = reserve the second spectrum buffer that the filter gradient of
      * fft2_filter_ifft2_backward needs (doubles the spectrum part of the

@@ -365,7 +365,9 @@ int fft_plan_set_option(gbfft_plan_t p, int key, int64_t value) {
             layout(p);
             return GBFFT_OK;
         case GBFFT_OPT_PRECISION:
-            if (value != 0) return value == 1 ? GBFFT_ERR_UNSUPPORTED : GBFFT_ERR_INVALID_VALUE;
+            if (value < 0 || value > 2) return GBFFT_ERR_INVALID_VALUE;
+            if (value != 0 && !(p->kind == KIND_2D && tc_supported(1 << p->log2r, 1 << p->log2c)))
+                return GBFFT_ERR_UNSUPPORTED;
             p->opt_precision = value;
             return GBFFT_OK;
         case GBFFT_OPT_IMAGES_PER_CHUNK:
@@ -486,8 +488,18 @@ static int pipeline_chunk(gbfft_plan *p, const float *img, const float *H, float
     a.scale = (float)(1.0 / ((double)rows * cols));
     a.tw = p->ws + p->off_tw0;
     const bool prep = per_image || first;  // a shared filter is prepared once per call
+    // with profiling on, the preparation runs on the caller's stream so that
+    // every kernel's events time that kernel alone
+    const bool side = prep && !p->opt_profile;
     int rc;
-    if (prep) {
+    if (prep && !side) {
+        rc = launch(p, GBFFT_STAGE_FILTER_PREP, s, [&] {
+            return launch_filter_prep(H, a.hs, a.beta, rows, cols, per_image ? nb : 1, a.scale, p->opt_h_stride,
+                                      per_image ? half_px : 0, per_image ? rows : 0, s);
+        });
+        if (rc) return rc;
+    }
+    if (side) {
         cudaError_t e = ensure_aux(p);
         if (e == cudaSuccess) e = cudaEventRecord(p->ev_fork, s);
         if (e == cudaSuccess) e = cudaStreamWaitEvent(p->aux, p->ev_fork, 0);
@@ -499,19 +511,26 @@ static int pipeline_chunk(gbfft_plan *p, const float *img, const float *H, float
         if (rc) return rc;
         if ((e = cudaEventRecord(p->ev_join, p->aux)) != cudaSuccess) return cuda_fail(e);
     }
-    rc = launch(p, GBFFT_STAGE_ROWS_FWD, s, [&] { return launch_rows_fwd(a, s); });
+    const int terms = p->opt_precision ? (int)p->opt_precision + 1 : 0;  // split-BF16 tensor-core passes
+    rc = launch(p, GBFFT_STAGE_ROWS_FWD, s, [&] {
+        return terms ? launch_rows_tc(true, img, a.spec, rows, cols, nb, a.tw, terms, s) : launch_rows_fwd(a, s);
+    });
     if (rc) return rc;
-    if (prep) {
+    if (side) {
         cudaError_t e = cudaStreamWaitEvent(s, p->ev_join, 0);
         if (e != cudaSuccess) return cuda_fail(e);
     }
+    const long long hs_img = per_image ? half_px : 0, beta_img = per_image ? rows : 0;
     rc = launch(p, GBFFT_STAGE_COLS, s, [&] {
-        return launch_cols_filter(a.spec, a.hs, a.beta, per_image ? half_px : 0, per_image ? rows : 0, rows, cols, nb,
-                                  p->ws + p->off_tw1, s);
+        return terms ? launch_cols_tc(a.spec, a.hs, a.beta, hs_img, beta_img, rows, cols, nb, p->ws + p->off_tw1, terms,
+                                      s)
+                     : launch_cols_filter(a.spec, a.hs, a.beta, hs_img, beta_img, rows, cols, nb, p->ws + p->off_tw1, s);
     });
     if (rc) return rc;
-    return launch(p, GBFFT_STAGE_ROWS_INV, s,
-                  [&] { return launch_rows_inv(a.spec, out, rows, cols, nb, p->ws + p->off_tw0, s); });
+    return launch(p, GBFFT_STAGE_ROWS_INV, s, [&] {
+        return terms ? launch_rows_tc(false, a.spec, out, rows, cols, nb, p->ws + p->off_tw0, terms, s)
+                     : launch_rows_inv(a.spec, out, rows, cols, nb, p->ws + p->off_tw0, s);
+    });
 }
 
 int fft2_filter_ifft2(gbfft_plan_t p, const float *img, const float *H, float *out, gbfft_stream_t stream) {
@@ -715,12 +734,16 @@ int fft_plan_autotune(gbfft_plan_t p, const void *args, gbfft_stream_t stream) {
     if (e == cudaSuccess) e = cudaEventCreate(&b);
     if (e != cudaSuccess) return cuda_fail(e);
     const int nsm = sm_count();
-    int grid[3];
+    int grid[3], fits[3] = {1, 1, 1};
+    // occupancy of every stage first: this also sets each kernel's shared
+    // memory attributes, which every launch below needs
     for (int st = 0; st < 3 && e == cudaSuccess; ++st) {
-        int fit = 0;
-        e = batch_max_blocks_per_sm(st, p->bsmem[st], &fit);
-        if (fit < 1) fit = 1;
-        for (int q = 0; q < 3; ++q) grid[q] = (p->opt_bps[q] > 0 ? (int)p->opt_bps[q] : fit) * nsm;
+        e = batch_max_blocks_per_sm(st, p->bsmem[st], &fits[st]);
+        if (fits[st] < 1) fits[st] = 1;
+    }
+    for (int st = 0; st < 3 && e == cudaSuccess; ++st) {
+        const int fit = fits[st];
+        for (int q = 0; q < 3; ++q) grid[q] = (p->opt_bps[q] > 0 ? (int)p->opt_bps[q] : fits[q]) * nsm;
         float best = 1e30f;
         int best_bps = fit;
         for (int bps = 1; bps <= fit && e == cudaSuccess; ++bps) {

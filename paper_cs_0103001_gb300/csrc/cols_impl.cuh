@@ -25,6 +25,7 @@
 #pragma once
 
 #include "fft_core.cuh"
+#include "fft_tc.cuh"
 #include "layout.cuh"
 
 namespace gbfft {
@@ -54,10 +55,10 @@ __device__ __forceinline__ int slot_e(int t, int e, int log2g) {
 // One block's share of the column pass: half-spectrum columns bx*W .. bx*W + W - 1
 // of one image.  spec: that image's half spectra [M/2][N] (slot order), hs /
 // beta: its prepared filter.
-template <int N>
+template <int N, typename FFT = Fp32Fft>
 __device__ __forceinline__ void cols_body(float2 *spec, const float *__restrict__ hs, const float *__restrict__ beta,
                                           int M, int log2g, const float2 *__restrict__ tw, int bx,
-                                          unsigned char *smraw) {
+                                          unsigned char *smraw, FFT fft = FFT()) {
     typedef ColCfg<N> K;
     constexpr int E = K::E, T = K::T, W = K::W;
     const int w = threadIdx.x / T;
@@ -74,7 +75,7 @@ __device__ __forceinline__ void cols_body(float2 *spec, const float *__restrict_
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = active ? col[slot_e<N, E, T>(t, e, log2g)] : make_float2(0.f, 0.f);
 
-    fft_regs<N, E, -1>(v, ex, tw, t);
+    fft.template run<N, E, -1>(v, ex, tw, t);
 
     // the filter is read after the forward transform so it holds no registers during it
     float h[E];
@@ -101,7 +102,7 @@ __device__ __forceinline__ void cols_body(float2 *spec, const float *__restrict_
         }
     }
 
-    fft_regs<N, E, 1>(v, ex, tw, t);
+    fft.template run<N, E, 1>(v, ex, tw, t);
 
     if (active) {
 #pragma unroll

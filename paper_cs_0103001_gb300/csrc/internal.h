@@ -65,6 +65,13 @@ cudaError_t launch_cols_filter(void *spec, const float *hs, const float *beta, l
                                int rows, int cols, int nimg, const void *tw_rows, cudaStream_t s);
 cudaError_t launch_rows_inv(const void *spec, float *out, int rows, int cols, int nimg, const void *tw_cols,
                             cudaStream_t s);
+// Tensor-core variants (tc2d.cu): radix-16 passes as split-BF16 DFT-matrix
+// products with `terms` = 2 or 3 BF16 parts per operand; sides 512..4096.
+bool tc_supported(int rows, int cols);
+cudaError_t launch_rows_tc(bool fwd, const void *src, void *dst, int rows, int cols, int nimg, const void *tw,
+                           int terms, cudaStream_t s);
+cudaError_t launch_cols_tc(void *spec, const float *hs, const float *beta, long long hs_img, long long beta_img,
+                           int rows, int cols, int nimg, const void *tw_rows, int terms, cudaStream_t s);
 // Adjoint column pass (cols_grad.cu): per column, loop over nimg images of
 // spec_x / spec_g, accumulate scale * sum Re(conj(W G) W x) into grad_T
 // [cols/2 + 1][rows] (slot order; added to its contents when `accumulate`),

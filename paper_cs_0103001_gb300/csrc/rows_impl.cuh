@@ -22,6 +22,7 @@
 #pragma once
 
 #include "fft_core.cuh"
+#include "fft_tc.cuh"
 #include "layout.cuh"
 
 namespace gbfft {
@@ -45,11 +46,12 @@ template <int M> struct RowCfg {
 // pairs from H (row-major [N][M]) into hs [M/2][N] and beta [N].  Every thread
 // of the block must call it; it ends after a block-wide barrier-free epilogue,
 // so a caller that reuses shared memory must synchronise first.
-template <int M>
+template <int M, typename FFT = Fp32Fft>
 __device__ __forceinline__ void rows_fwd_body(const float *__restrict__ img, float2 *__restrict__ spec,
                                               const float *__restrict__ H, float *__restrict__ hs,
                                               float *__restrict__ beta, int N, int log2g, bool prep, float scale,
-                                              const float2 *__restrict__ tw, int bx, unsigned char *smraw) {
+                                              const float2 *__restrict__ tw, int bx, unsigned char *smraw,
+                                              FFT fft = FFT()) {
     typedef RowCfg<M> K;
     constexpr int E = K::E, T = K::T, SR = K::SR, H2 = M / 2;
     float2 *sm = reinterpret_cast<float2 *>(smraw);
@@ -72,7 +74,7 @@ __device__ __forceinline__ void rows_fwd_body(const float *__restrict__ img, flo
         for (int e = 0; e < E; ++e) v[e] = make_float2(0.f, 0.f);
     }
     float2 *ex = sm + g * padded_len(M);
-    fft_regs<M, E, -1>(v, ex, tw, t);
+    fft.template run<M, E, -1>(v, ex, tw, t);
     __syncthreads();
 #pragma unroll
     for (int e = 0; e < E; ++e) ex[pad16(t + T * e)] = v[e];
@@ -153,10 +155,10 @@ __device__ __forceinline__ void rows_fwd_body(const float *__restrict__ img, flo
 
 // One block's share of the inverse row pass: spec [M/2][N] (slot order) of one
 // image -> rows of pairs bx*G .. bx*G + G - 1 of out [N][M], unscaled.
-template <int M>
+template <int M, typename FFT = Fp32Fft>
 __device__ __forceinline__ void rows_inv_body(const float2 *__restrict__ spec, float *__restrict__ out, int N,
                                               int log2g, const float2 *__restrict__ tw, int bx,
-                                              unsigned char *smraw) {
+                                              unsigned char *smraw, FFT fft = FFT()) {
     typedef RowCfg<M> K;
     constexpr int E = K::E, T = K::T, SR = K::SR, H2 = M / 2;
     float2 *sm = reinterpret_cast<float2 *>(smraw);
@@ -210,7 +212,7 @@ __device__ __forceinline__ void rows_inv_body(const float2 *__restrict__ spec, f
     }
     // the exchange buffers overlap the staging area: the first exchange of
     // fft_regs starts with a block barrier, after every thread read its values
-    fft_regs<M, E, 1>(v, sm + g * padded_len(M), tw, t);
+    fft.template run<M, E, 1>(v, sm + g * padded_len(M), tw, t);
     if (active) {
         float *ra = out + (size_t)a * M;
         float *rb = out + (size_t)b * M;

@@ -110,3 +110,25 @@ def test_uneven_workload_sampled():
         if i % 5 == 0:
             ref = gb.fft2_filter_ifft2(a, h)
             assert rel_l2(outs[i].cpu().numpy(), ref.cpu().numpy()) <= tol_fp32(a.numel())
+
+
+def test_autotune_first_in_a_fresh_process():
+    """Tuning before any other batched call (so no kernel attribute has been
+    set yet in the process) must work."""
+    import os
+    import subprocess
+    import sys
+
+    code = (
+        "import torch, paper_cs_0103001_gb300 as gb\n"
+        "from paper_cs_0103001_gb300 import synth\n"
+        "b = synth.uneven_batch(12, 7)\n"
+        "ti = [torch.from_numpy(a).cuda() for a, _, _ in b]\n"
+        "th = [torch.from_numpy(h).cuda() for _, h, _ in b]\n"
+        "p = gb.Plan2DBatched([tuple(a.shape) for a in ti], 'cuda')\n"
+        "print(p.autotune(ti, th))\n"
+    )
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, timeout=600,
+                       env={**os.environ, "PYTHONPATH": root})
+    assert r.returncode == 0, r.stderr[-2000:]
