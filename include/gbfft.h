@@ -107,7 +107,14 @@ typedef enum {
     /* Batched plans: 1 (default) = capture the three stage launches in a CUDA
      * graph on the first call and replay it while the image-pointer array and
      * the launch shapes stay the same; 0 = plain launches. */
-    GBFFT_OPT_USE_GRAPH = 8
+    GBFFT_OPT_USE_GRAPH = 8,
+    /* 2D plans with both sides 16..256: 1 (default) = run the whole pipeline
+     * of fft2_filter_ifft2 in one launch per chunk, one thread-block cluster
+     * per image holding the image's half spectra in shared memory (the
+     * spectrum never goes to global memory); 0 = the three-pass path
+     * (rows, columns, inverse rows) used for larger images.  Same result up
+     * to rounding order.  Ignored with GBFFT_OPT_PRECISION != 0. */
+    GBFFT_OPT_ONCHIP = 9
 } gbfft_option;
 
 /* Stages reported by gbfft_plan_profile_read. */
@@ -122,7 +129,8 @@ typedef enum {
     GBFFT_STAGE_TWIDDLES = 7,  /* twiddle-table generation (bind time) */
     GBFFT_STAGE_GRAPH = 8,     /* one replay of a batched plan's captured graph */
     GBFFT_STAGE_FILTER_PREP = 9, /* 2D: even part of the filter, slot order (side stream) */
-    GBFFT_STAGE_COUNT = 10
+    GBFFT_STAGE_ONCHIP = 10,   /* 2D small images: the whole pipeline in one cluster launch */
+    GBFFT_STAGE_COUNT = 11
 } gbfft_stage;
 
 /* ---- plans --------------------------------------------------------------- */

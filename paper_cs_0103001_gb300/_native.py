@@ -38,10 +38,11 @@ OPT_PROFILE = 5
 OPT_ENABLE_BACKWARD = 6
 OPT_BLOCKS_PER_SM = 7
 OPT_USE_GRAPH = 8
+OPT_ONCHIP = 9
 
 # gbfft_stage
 STAGES = ("fft1d", "fourstep_a", "fourstep_b", "rows_fwd", "cols_filter", "rows_inv", "cols_grad", "twiddles",
-          "graph", "filter_prep")
+          "graph", "filter_prep", "onchip")
 
 # every exported symbol with (restype, argtypes)
 _P = ctypes.c_void_p

@@ -63,6 +63,7 @@ struct gbfft_plan {
     size_t bsmem[3] = {0, 0, 0};
     int64_t opt_bps[3] = {0, 0, 0};  // blocks per SM per stage (0 = as many as fit)
     int64_t opt_graph = 1;
+    int64_t opt_onchip = 1;
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
@@ -389,6 +390,10 @@ int fft_plan_set_option(gbfft_plan_t p, int key, int64_t value) {
             p->opt_graph = value;
             drop_graph(p);
             return GBFFT_OK;
+        case GBFFT_OPT_ONCHIP:
+            if (p->kind != KIND_2D || (value != 0 && value != 1)) return GBFFT_ERR_INVALID_VALUE;
+            p->opt_onchip = value;
+            return GBFFT_OK;
         case GBFFT_OPT_ENABLE_BACKWARD:
             if (p->kind != KIND_2D || (value != 0 && value != 1)) return GBFFT_ERR_INVALID_VALUE;
             p->opt_backward = value;
@@ -487,6 +492,13 @@ static int pipeline_chunk(gbfft_plan *p, const float *img, const float *H, float
     a.filter_mode = 0;  // prepared separately below
     a.scale = (float)(1.0 / ((double)rows * cols));
     a.tw = p->ws + p->off_tw0;
+    const int terms = p->opt_precision ? (int)p->opt_precision + 1 : 0;  // split-BF16 tensor-core passes
+    if (!terms && p->opt_onchip && onchip_supported(rows, cols)) {
+        return launch(p, GBFFT_STAGE_ONCHIP, s, [&] {
+            return launch_onchip(img, H, out, p->opt_h_stride, rows, cols, nb, p->ws + p->off_tw0,
+                                 p->ws + p->off_tw1, s);
+        });
+    }
     const bool prep = per_image || first;  // a shared filter is prepared once per call
     // with profiling on, the preparation runs on the caller's stream so that
     // every kernel's events time that kernel alone
@@ -511,7 +523,6 @@ static int pipeline_chunk(gbfft_plan *p, const float *img, const float *H, float
         if (rc) return rc;
         if ((e = cudaEventRecord(p->ev_join, p->aux)) != cudaSuccess) return cuda_fail(e);
     }
-    const int terms = p->opt_precision ? (int)p->opt_precision + 1 : 0;  // split-BF16 tensor-core passes
     rc = launch(p, GBFFT_STAGE_ROWS_FWD, s, [&] {
         return terms ? launch_rows_tc(true, img, a.spec, rows, cols, nb, a.tw, terms, s) : launch_rows_fwd(a, s);
     });
@@ -791,6 +802,7 @@ int fft_plan_get_option(gbfft_plan_t p, int key, int64_t *value) {
             *value = p->opt_bps[0] | (p->opt_bps[1] << 8) | (p->opt_bps[2] << 16);
             return GBFFT_OK;
         case GBFFT_OPT_USE_GRAPH: *value = p->opt_graph; return GBFFT_OK;
+        case GBFFT_OPT_ONCHIP: *value = p->opt_onchip; return GBFFT_OK;
         default: return GBFFT_ERR_INVALID_VALUE;
     }
 }

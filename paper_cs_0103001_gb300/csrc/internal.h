@@ -68,6 +68,9 @@ cudaError_t launch_rows_inv(const void *spec, float *out, int rows, int cols, in
 // Tensor-core variants (tc2d.cu): radix-16 passes as split-BF16 DFT-matrix
 // products with `terms` = 2 or 3 BF16 parts per operand; sides 512..4096.
 bool tc_supported(int rows, int cols);
+bool onchip_supported(int rows, int cols);
+cudaError_t launch_onchip(const float *img, const float *H, float *out, long long h_stride, int rows, int cols,
+                          int nimg, const void *tw_cols, const void *tw_rows, cudaStream_t s);
 cudaError_t launch_rows_tc(bool fwd, const void *src, void *dst, int rows, int cols, int nimg, const void *tw,
                            int terms, cudaStream_t s);
 cudaError_t launch_cols_tc(void *spec, const float *hs, const float *beta, long long hs_img, long long beta_img,

@@ -1,0 +1,124 @@
+"""GPU parity of the one-launch small-image pipeline (both sides 16..256: one
+thread-block cluster per image, half spectra in shared memory) against the
+FP64 oracle and against the three-pass path, through the C ABI."""
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_cs_0103001_gb300 import synth
+from tests.gpu_util import max_rel_l2, rel_l2, tol_fp32
+
+pytestmark = pytest.mark.gpu
+
+SIDES = [16, 32, 64, 128, 256]
+
+
+@pytest.fixture(scope="module")
+def gb():
+    import torch
+
+    import paper_cs_0103001_gb300 as gb
+
+    assert torch.cuda.is_available()
+    return gb
+
+
+def _run(gb, img, H, onchip, h_stride=0):
+    import torch
+
+    from paper_cs_0103001_gb300 import _native as nat
+
+    B, rows, cols = img.shape
+    plan = gb.Plan2D(rows, cols, B, "cuda", {nat.OPT_ONCHIP: onchip, nat.OPT_PROFILE: 1,
+                                             nat.OPT_H_BATCH_STRIDE: h_stride})
+    out = torch.empty(img.shape, dtype=torch.float32, device="cuda")
+    plan.filter(torch.from_numpy(img).cuda(), torch.from_numpy(H).cuda(), out=out)
+    torch.cuda.synchronize()
+    prof = plan.profile_read()
+    return out.cpu().numpy(), prof
+
+
+@pytest.mark.parametrize("rows", SIDES)
+@pytest.mark.parametrize("cols", SIDES)
+def test_all_shapes_against_oracle_and_three_pass(gb, rows, cols):
+    """Every on-chip shape, a filter with no symmetry, two images; the launch
+    list shows the single on-chip kernel, the three-pass path agrees."""
+    img = np.stack([synth.sky(rows, cols, max(2, rows * cols // 1000), 40, rows, cols, b) for b in range(2)])
+    H = synth.random_filter(rows, cols, 41, rows, cols)
+    ref = oracle.pipeline(img, H)
+    tol = tol_fp32(rows * cols)
+    out, prof = _run(gb, img, H, 1)
+    assert prof["onchip"][1] == 1 and not {"rows_fwd", "cols_filter", "rows_inv", "filter_prep"} & set(prof)
+    assert max_rel_l2(out, ref, axes=(1, 2)) <= tol
+    out3, prof3 = _run(gb, img, H, 0)
+    assert "onchip" not in prof3 and "cols_filter" in prof3
+    assert max_rel_l2(out3, ref, axes=(1, 2)) <= tol
+    assert max_rel_l2(out, out3, axes=(1, 2)) <= 2 * tol
+
+
+def test_per_image_filters_many_clusters(gb):
+    """300 images of 64 x 128, each with its own Gaussian: 300 clusters in one
+    launch, image b must use filter b."""
+    rows, cols, B = 64, 128, 300
+    img = np.stack([synth.sky(rows, cols, 8, 42, b) for b in range(B)])
+    H = np.stack([synth.gaussian_lowpass(rows, cols, 2.0 + 0.1 * b) for b in range(B)])
+    out, prof = _run(gb, img, H, 1, h_stride=rows * cols)
+    assert prof["onchip"][1] == 1
+    assert max_rel_l2(out, oracle.pipeline(img, H), axes=(1, 2)) <= tol_fp32(rows * cols)
+
+
+def test_workload_256_gaussian32(gb):
+    """The 256^2 sky (50 sources) with the sigma = 32 Gaussian low-pass."""
+    img = synth.sky(256, 256, 50, 0)[None]
+    H = synth.gaussian_lowpass(256, 256, 32.0)
+    out, _ = _run(gb, img, H, 1)
+    assert rel_l2(out[0], oracle.pipeline(img[0], H)) <= tol_fp32(256 * 256)
+
+
+def test_closed_forms(gb):
+    """H = 1 returns the image; H = delta at DC returns its mean everywhere;
+    a filter that keeps one wrapped frequency pair of a pure cosine image keeps it."""
+    rows, cols = 128, 256
+    img = synth.sky(rows, cols, 30, 43)[None]
+    out, _ = _run(gb, img, np.ones((rows, cols), np.float32), 1)
+    assert rel_l2(out[0], img[0].astype(np.float64)) <= tol_fp32(rows * cols)
+    d = np.zeros((rows, cols), np.float32)
+    d[0, 0] = 1
+    out, _ = _run(gb, img, d, 1)
+    assert np.max(np.abs(out[0] - img[0].astype(np.float64).mean())) <= 1e-5 * abs(img.mean())
+    y, x = np.mgrid[0:rows, 0:cols]
+    cosimg = np.cos(2 * np.pi * (3 * y / rows + 5 * x / cols)).astype(np.float32)[None]
+    keep = np.zeros((rows, cols), np.float32)
+    keep[3, 5] = keep[rows - 3, cols - 5] = 1
+    out, _ = _run(gb, cosimg, keep, 1)
+    assert np.max(np.abs(out[0] - cosimg[0])) <= 1e-5
+    keep[3, 5] = keep[rows - 3, cols - 5] = 0
+    keep[4, 5] = 1
+    out, _ = _run(gb, cosimg, keep, 1)
+    assert np.max(np.abs(out[0])) <= 1e-5
+
+
+@pytest.mark.parametrize("rows,cols", [(128, 256), (512, 512)])
+def test_graph_capture_replay(gb, rows, cols):
+    """fft2_filter_ifft2 captured in a CUDA graph (the on-chip launch, and the
+    three-pass path with its side-stream filter preparation) replays to the
+    eager result on new inputs written into the captured buffers."""
+    import torch
+
+    plan = gb.Plan2D(rows, cols, 1, "cuda")
+    img = torch.from_numpy(synth.sky(rows, cols, 20, 44)).cuda()
+    H = torch.from_numpy(synth.gaussian_lowpass(rows, cols, 9.0)).cuda()
+    out = torch.empty_like(img)
+    plan.filter(img, H, out=out)  # first call outside the capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        plan.filter(img, H, out=out)
+    img2 = synth.sky(rows, cols, 20, 45)
+    H2 = synth.random_filter(rows, cols, 46)
+    img.copy_(torch.from_numpy(img2))
+    H.copy_(torch.from_numpy(H2))
+    g.replay()
+    torch.cuda.synchronize()
+    assert rel_l2(out.cpu().numpy(), oracle.pipeline(img2, H2)) <= tol_fp32(rows * cols)
