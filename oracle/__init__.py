@@ -211,6 +211,44 @@ def spectrum(F) -> np.ndarray:
 
 
 # --------------------------------------------------------------------------
+# Sec. 5's application path for an image whose sides are not powers of two:
+# the image is enlarged with zeros to power-of-two sides before the transform,
+# and the filtered result is cut back to the original size.  Where the zeros
+# go is not stated; they are appended after the last row and the last column.
+# --------------------------------------------------------------------------
+
+def pad(img, rows: int, cols: int) -> np.ndarray:
+    """Zero-extend [..., r, c] to [..., rows, cols] (zeros after the last row
+    and after the last column); float64."""
+    img = np.asarray(img, dtype=np.float64)
+    r, c = img.shape[-2:]
+    if r > rows or c > cols:
+        raise ValueError("image larger than the padded size")
+    out = np.zeros(img.shape[:-2] + (rows, cols))
+    out[..., :r, :c] = img
+    return out
+
+
+def crop(x, rows: int, cols: int) -> np.ndarray:
+    """The first `rows` rows and `cols` columns of [..., R, C]."""
+    return np.array(np.asarray(x)[..., :rows, :cols])
+
+
+def pipeline_padded(img, H, conv: int = PER_AXIS) -> np.ndarray:
+    """Sec. 5 on a zero-padded image: crop(pipeline(pad(img), H)).  H is given
+    on the padded grid ([R, C] shared, or [..., R, C] per image)."""
+    img = np.asarray(img, dtype=np.float64)
+    R, C = np.asarray(H).shape[-2:]
+    return crop(pipeline(pad(img, R, C), H, conv), img.shape[-2], img.shape[-1])
+
+
+def spectrum_padded(img, rows: int, cols: int, conv: int = PER_AXIS) -> np.ndarray:
+    """Sec. 5 spectrum display of the zero-padded image: |fft2(pad(img))| on
+    the rows x cols grid, in natural (unshifted) order."""
+    return spectrum(fft2(pad(img, rows, cols), conv))
+
+
+# --------------------------------------------------------------------------
 # The paper's bookkeeping (pure Python, tiny inputs only).
 # --------------------------------------------------------------------------
 

@@ -199,6 +199,58 @@ def pin_pipeline(orc):
     assert rel_l2(orc.pipeline(img, Hs), each) < TOL
 
 
+def pin_padded_pipeline(orc):
+    """Zero padding to power-of-two sides, filter, crop (Sec. 5 application):
+    brute force with the zeros written out by hand, identity and power-of-two
+    special cases."""
+    g = _rng(71)
+    for (r, c), (R, C) in (((5, 6), (8, 8)), ((3, 7), (4, 8)), ((6, 3), (8, 4))):
+        img = g.normal(size=(r, c))
+        H = g.uniform(0, 2, size=(R, C))
+        big = np.zeros((R, C))
+        for i in range(r):
+            for j in range(c):
+                big[i, j] = img[i, j]
+        want = circular_filter_direct(big, H)[:r, :c]
+        got = orc.pipeline_padded(img, H)
+        assert got.shape == (r, c) and rel_l2(got, want) < TOL, (r, c)
+    img = g.normal(size=(2, 13, 21))
+    assert rel_l2(orc.pipeline_padded(img, np.ones((16, 32))), img) < TOL  # H == 1
+    img = g.normal(size=(16, 8))
+    H = g.uniform(0, 2, size=(16, 8))
+    assert rel_l2(orc.pipeline_padded(img, H), orc.pipeline(img, H)) < TOL  # nothing to pad
+    # per-image filters on the padded grid
+    img = g.normal(size=(3, 5, 6))
+    Hs = g.uniform(0, 2, size=(3, 8, 8))
+    each = np.stack([orc.pipeline_padded(img[b], Hs[b]) for b in range(3)])
+    assert rel_l2(orc.pipeline_padded(img, Hs), each) < TOL
+
+
+def pin_spectrum(orc):
+    """Spectrum display |F| of the padded image: closed forms (delta, constant,
+    one cosine), Parseval with the 1/(N M) scale, the Hermitian mirror, and
+    Eq. 5's factor M."""
+    R, C = 8, 16
+    d = np.zeros((5, 11))
+    d[0, 0] = 1
+    s = orc.spectrum_padded(d, R, C)
+    assert s.shape == (R, C) and np.max(np.abs(s - 1.0 / (R * C))) < 1e-15
+    s = orc.spectrum_padded(np.full((5, 11), 3.0), R, C)
+    assert abs(s[0, 0] - 3.0 * 55 / (R * C)) < 1e-14
+    y, x = np.mgrid[0:R, 0:C]
+    s = orc.spectrum_padded(np.cos(2 * np.pi * (2 * y / R + 3 * x / C)), R, C)
+    want = np.zeros((R, C))
+    want[2, 3] = want[R - 2, C - 3] = 0.5
+    assert np.max(np.abs(s - want)) < 1e-14
+    g = _rng(72)
+    img = g.normal(size=(7, 13))
+    s = orc.spectrum_padded(img, R, C)
+    assert abs(np.sum(s * s) - np.sum(img * img) / (R * C)) < 1e-12 * np.sum(img * img)
+    mirror = s[(-np.arange(R)) % R][:, (-np.arange(C)) % C]
+    assert np.max(np.abs(s - mirror)) < 1e-14
+    assert rel_l2(orc.spectrum_padded(img, R, C, 1), C * s) < TOL
+
+
 def pin_pipeline_grad(orc, rows=8, cols=16, batch=2, probes=12):
     """Central finite differences of L = sum(y * G): the loss is linear in img
     (for fixed H) and in H (for fixed img), so the difference is exact up to
@@ -278,4 +330,6 @@ ALL_PINS = [
     pin_pipeline_grad,
     pin_table1,
     pin_tree_example,
+    pin_padded_pipeline,
+    pin_spectrum,
 ]

@@ -63,7 +63,25 @@ MUTANTS = {
         oracle.table1_row(n, nproc)[4])),
     # leaves in natural order instead of bit-reversed
     "leaves_natural": dict(tree_leaf_order=lambda n: list(range(n))),
+    # zeros put before the image (top-left) but the result cut from the top-left corner
+    "pad_before_crop_after": dict(pipeline_padded=lambda img, H, conv=0: _pad_before(img, H, conv)),
+    # result cut from the wrong corner of the padded grid
+    "crop_wrong_corner": dict(pipeline_padded=lambda img, H, conv=0: np.asarray(oracle.pipeline(
+        oracle.pad(img, *np.asarray(H).shape[-2:]), H, conv))[..., -np.shape(img)[-2]:, -np.shape(img)[-1]:]),
+    # squared magnitude instead of sqrt(Re^2 + Im^2)
+    "spectrum_squared": dict(spectrum_padded=lambda img, R, C, conv=0: oracle.spectrum_padded(img, R, C, conv) ** 2),
+    # spectrum of the unscaled transform
+    "spectrum_unscaled": dict(spectrum_padded=lambda img, R, C, conv=0: oracle.spectrum_padded(img, R, C, conv) * R * C),
 }
+
+
+def _pad_before(img, H, conv):
+    img = np.asarray(img, dtype=np.float64)
+    R, C = np.asarray(H).shape[-2:]
+    r, c = img.shape[-2:]
+    big = np.zeros(img.shape[:-2] + (R, C))
+    big[..., R - r:, C - c:] = img
+    return oracle.pipeline(big, H, conv)[..., :r, :c]
 
 
 @pytest.mark.parametrize("name", sorted(MUTANTS))
