@@ -495,6 +495,25 @@ def variant_pipeline256(steps: int = 200):
     return res
 
 
+def variant_paper_application(steps: int = 200):
+    """Sec. 5's own configuration: a 460 x 506 sky zero-padded to 512^2, the
+    disc filter of radius 340, the result cut back to 460 x 506; and the
+    spectrum display of the padded image (median call latency, inputs in L2)."""
+    import torch
+
+    import paper_cs_0103001_gb300 as gb
+    from paper_cs_0103001_gb300 import synth
+
+    img = torch.from_numpy(synth.sky(460, 506, 200, 6)).cuda()
+    H = torch.from_numpy(synth.disc_filter(512, 512, 340.0)).cuda()
+    plan = gb.Plan2D(512, 512, 1, "cuda")
+    out = torch.empty_like(img)
+    mag = torch.empty(512, 512, device="cuda")
+    ms_f = _timed(lambda: plan.filter_padded(img, H, out=out), steps, 20)
+    ms_s = _timed(lambda: plan.spectrum(img, out=mag), steps, 20)
+    return {"filter_us": round(ms_f * 1e3, 2), "spectrum_us": round(ms_s * 1e3, 2)}
+
+
 def variant_backward(steps: int = 5):
     """16 x 2048^2 noisy skies, learnable filter (init 1): forward and adjoint."""
     import torch
@@ -528,7 +547,8 @@ def run_variants():
                      ("fft1d_c64_2^16", lambda: variant_fft1d(16)), ("fft1d_c64_2^20", lambda: variant_fft1d(20)),
                      ("fft1d_c64_2^24", lambda: variant_fft1d(24)),
                      ("fft1d_c128_2^20x64", lambda: variant_fft1d(20, "c128", 3)),
-                     ("pipeline_256", variant_pipeline256), ("backward_16x2048", variant_backward),
+                     ("pipeline_256", variant_pipeline256), ("paper_application_460x506", variant_paper_application),
+                     ("backward_16x2048", variant_backward),
                      ("batched_uneven_512", variant_batched)):
         out[name] = _guard(fn)
         torch.cuda.empty_cache()

@@ -108,12 +108,14 @@ typedef enum {
      * graph on the first call and replay it while the image-pointer array and
      * the launch shapes stay the same; 0 = plain launches. */
     GBFFT_OPT_USE_GRAPH = 8,
-    /* 2D plans with both sides 16..256: 1 (default) = run the whole pipeline
-     * of fft2_filter_ifft2 in one launch per chunk, one thread-block cluster
-     * per image holding the image's half spectra in shared memory (the
-     * spectrum never goes to global memory); 0 = the three-pass path
-     * (rows, columns, inverse rows) used for larger images.  Same result up
-     * to rounding order.  Ignored with GBFFT_OPT_PRECISION != 0. */
+    /* 1 (default) = use the one-launch cluster paths where they apply;
+     * 0 = the multi-pass paths.  2D plans with both sides 16..256: the whole
+     * pipeline of fft2_filter_ifft2 in one launch, one thread-block cluster
+     * per image holding its half spectra in shared memory (ignored with
+     * GBFFT_OPT_PRECISION != 0).  1D complex64 plans of length 2^15..2^17:
+     * one cluster per transform, the four-step intermediate in distributed
+     * shared memory (one HBM read and one write instead of two each).  Same
+     * results up to rounding order. */
     GBFFT_OPT_ONCHIP = 9
 } gbfft_option;
 
@@ -130,7 +132,9 @@ typedef enum {
     GBFFT_STAGE_GRAPH = 8,     /* one replay of a batched plan's captured graph */
     GBFFT_STAGE_FILTER_PREP = 9, /* 2D: even part of the filter, slot order (side stream) */
     GBFFT_STAGE_ONCHIP = 10,   /* 2D small images: the whole pipeline in one cluster launch */
-    GBFFT_STAGE_COUNT = 11
+    GBFFT_STAGE_SPECTRUM = 11, /* 2D spectrum display: column FFTs, magnitudes, row-major write */
+    GBFFT_STAGE_FFT1D_CLUSTER = 12, /* 1D 2^15..2^17: one thread-block cluster per transform */
+    GBFFT_STAGE_COUNT = 13
 } gbfft_stage;
 
 /* ---- plans --------------------------------------------------------------- */
@@ -178,6 +182,29 @@ int fft_inverse(gbfft_plan_t plan, const void *in, void *out, gbfft_stream_t str
  * stream of the plan, forked from and joined back to `stream` with events,
  * so the call stays ordered on `stream` (and can be captured in a graph). */
 int fft2_filter_ifft2(gbfft_plan_t plan, const float *img, const float *H, float *out, gbfft_stream_t stream);
+
+/* Sec. 5's application path for images whose sides are not powers of two:
+ * each of the plan's `batch` images is in_rows x in_cols float32 (row-major,
+ * contiguous, image b at img + b * in_rows * in_cols), 1 <= in_rows <= rows,
+ * 1 <= in_cols <= cols of the plan.  The image is zero-padded to the plan's
+ * rows x cols grid (zeros after its last row and last column), filtered as in
+ * fft2_filter_ifft2 with H (rows x cols, on the padded grid, 16-byte aligned;
+ * h_batch_stride applies), and the in_rows x in_cols top-left corner of the
+ * result is written to out (same layout as img).  img and out need only
+ * 4-byte alignment; img == out is allowed.  GBFFT_ERR_INVALID_SIZE for sizes
+ * out of range; GBFFT_ERR_UNSUPPORTED with GBFFT_OPT_PRECISION != 0. */
+int fft2_filter_ifft2_padded(gbfft_plan_t plan, const float *img, int64_t in_rows, int64_t in_cols, const float *H,
+                             float *out, gbfft_stream_t stream);
+
+/* Spectrum display of Sec. 5: mag = sqrt(Re^2 + Im^2) of the 2D transform of
+ * each image, zero-padded to the plan's grid as in fft2_filter_ifft2_padded
+ * (in_rows = rows, in_cols = cols for no padding).  mag: batch x rows x cols
+ * float32, natural (unshifted) frequency order, scaled per the plan's
+ * GBFFT_OPT_SCALE_CONVENTION (per-axis: the DFT divided by rows * cols;
+ * Eq. 5: by rows only).  Uses the plan's prepared-filter workspace as scratch:
+ * a following fft2_filter_ifft2 prepares its filter again as usual. */
+int fft2_spectrum(gbfft_plan_t plan, const float *img, int64_t in_rows, int64_t in_cols, float *mag,
+                  gbfft_stream_t stream);
 
 /* Adjoint of fft2_filter_ifft2 for an upstream gradient grad_out = dL/dout
  * (derived from Sec. 4's 2D-DFT and Sec. 5's filter; the paper has no

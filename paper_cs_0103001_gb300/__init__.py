@@ -20,8 +20,10 @@ from .api import (  # noqa: F401
     fft,
     fft2_filter_ifft2,
     fft2_filter_ifft2_batched,
+    fft2_filter_ifft2_padded,
+    fft2_spectrum,
     ifft,
 )
 
-__all__ = ["fft", "ifft", "fft2_filter_ifft2", "fft2_filter_ifft2_batched", "Plan1D", "Plan2D", "Plan2DBatched",
-           "clear_plan_cache"]
+__all__ = ["fft", "ifft", "fft2_filter_ifft2", "fft2_filter_ifft2_batched", "fft2_filter_ifft2_padded",
+           "fft2_spectrum", "Plan1D", "Plan2D", "Plan2DBatched", "clear_plan_cache"]

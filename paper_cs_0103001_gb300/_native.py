@@ -42,7 +42,7 @@ OPT_ONCHIP = 9
 
 # gbfft_stage
 STAGES = ("fft1d", "fourstep_a", "fourstep_b", "rows_fwd", "cols_filter", "rows_inv", "cols_grad", "twiddles",
-          "graph", "filter_prep", "onchip")
+          "graph", "filter_prep", "onchip", "spectrum", "fft1d_cluster")
 
 # every exported symbol with (restype, argtypes)
 _P = ctypes.c_void_p
@@ -57,6 +57,8 @@ SIGNATURES = {
     "fft_forward": (_INT, [_P, _P, _P, _P]),
     "fft_inverse": (_INT, [_P, _P, _P, _P]),
     "fft2_filter_ifft2": (_INT, [_P, _P, _P, _P, _P]),
+    "fft2_filter_ifft2_padded": (_INT, [_P, _P, _I64, _I64, _P, _P, _P]),
+    "fft2_spectrum": (_INT, [_P, _P, _I64, _I64, _P, _P]),
     "fft2_filter_ifft2_backward": (_INT, [_P, _P, _P, _P, _P, _P, _P]),
     "fft_plan_destroy": (_INT, [_P]),
     "fft2_batched_plan_create": (_INT, [_INT, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_P)]),

@@ -6,6 +6,8 @@ raw device pointers.  Functions here:
 
   fft(x), ifft(x)           1D transforms over the last axis (Eq. E2 / Eq. E3)
   fft2_filter_ifft2(img, H) the Sec. 5 pipeline, differentiable in img and H
+  fft2_filter_ifft2_padded  the same for any image size (zero padding, crop)
+  fft2_spectrum(img)        the Sec. 5 spectrum display |fft2(img)|
   Plan1D, Plan2D            explicit plans (workspace owned by a torch tensor)
 """
 
@@ -114,6 +116,26 @@ class Plan2D(_PlanBase):
             out = torch.empty_like(img)
         with self.lock:
             nat.call("fft2_filter_ifft2", self.handle, _ptr(img), _ptr(H), _ptr(out), _stream_handle(img.device))
+        return out
+
+    def filter_padded(self, img: torch.Tensor, H: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        """Images [..., r, c] with r <= rows, c <= cols, zero-padded to the
+        plan's grid, filtered with H (on the grid), cut back to r x c."""
+        if out is None:
+            out = torch.empty_like(img)
+        with self.lock:
+            nat.call("fft2_filter_ifft2_padded", self.handle, _ptr(img), int(img.shape[-2]), int(img.shape[-1]),
+                     _ptr(H), _ptr(out), _stream_handle(img.device))
+        return out
+
+    def spectrum(self, img: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        """|fft2| of images [..., r, c] zero-padded to the plan's grid:
+        [..., rows, cols] float32 in natural frequency order."""
+        if out is None:
+            out = torch.empty(img.shape[:-2] + (self.rows, self.cols), dtype=torch.float32, device=img.device)
+        with self.lock:
+            nat.call("fft2_spectrum", self.handle, _ptr(img), int(img.shape[-2]), int(img.shape[-1]), _ptr(out),
+                     _stream_handle(img.device))
         return out
 
     def backward(self, img, H, grad_out, grad_img=None, grad_H=None):
@@ -277,6 +299,48 @@ def fft2_filter_ifft2_batched(imgs, Hs):
     shapes = tuple((int(a.shape[-2]), int(a.shape[-1])) for a in imgs)
     plan = _cached(("batched", shapes, dev), lambda: Plan2DBatched(shapes, dev))
     return plan.filter([a.contiguous() for a in imgs], [h.contiguous() for h in Hs])
+
+
+def _next_pow2(n: int) -> int:
+    return 1 << max(0, int(n) - 1).bit_length()
+
+
+def fft2_filter_ifft2_padded(img: torch.Tensor, H: torch.Tensor) -> torch.Tensor:
+    """Sec. 5 application path for any image size: float32 images
+    [..., r, c] are zero-padded (after the last row and column) to the filter's
+    grid H [R, C] (powers of two, R >= r, C >= c; or one filter per image,
+    [..., R, C]), filtered, and cut back to r x c.  Not differentiable."""
+    _require_cuda(img, "img")
+    _require_cuda(H, "H")
+    if img.dtype != torch.float32 or H.dtype != torch.float32 or img.dim() < 2:
+        raise TypeError("img and H must be float32, img [..., rows, cols]")
+    R, C = int(H.shape[-2]), int(H.shape[-1])
+    per_image = H.dim() > 2
+    if per_image and H.shape[:-2] != img.shape[:-2]:
+        raise ValueError("per-image filters must match the batch dimensions of img")
+    r, c = int(img.shape[-2]), int(img.shape[-1])
+    batch = img.numel() // (r * c)
+    opts = {nat.OPT_H_BATCH_STRIDE: R * C if per_image else 0}
+    plan = _cached(("2dpad", R, C, batch, per_image, img.device), lambda: Plan2D(R, C, batch, img.device, opts))
+    return plan.filter_padded(img.contiguous(), H.contiguous())
+
+
+def fft2_spectrum(img: torch.Tensor, rows: int | None = None, cols: int | None = None,
+                  eq5: bool = False) -> torch.Tensor:
+    """Spectrum display of Sec. 5: sqrt(Re^2 + Im^2) of the 2D transform of
+    float32 images [..., r, c] zero-padded to rows x cols (default: the next
+    powers of two), natural frequency order; per-axis scale (the DFT divided by
+    rows * cols), or Eq. 5's (divided by rows) with eq5=True."""
+    _require_cuda(img, "img")
+    if img.dtype != torch.float32 or img.dim() < 2:
+        raise TypeError("img must be float32 [..., rows, cols]")
+    r, c = int(img.shape[-2]), int(img.shape[-1])
+    R = int(rows) if rows is not None else _next_pow2(r)
+    C = int(cols) if cols is not None else _next_pow2(c)
+    batch = img.numel() // (r * c)
+    opts = {nat.OPT_SCALE_CONVENTION: 1 if eq5 else 0}
+    plan = _cached(("2dspec", R, C, batch, bool(eq5), img.device), lambda: Plan2D(R, C, batch, img.device, opts))
+    return plan.spectrum(img.contiguous())
 
 
 def fft2_filter_ifft2(img: torch.Tensor, H: torch.Tensor) -> torch.Tensor:

@@ -50,7 +50,7 @@ struct gbfft_plan {
     size_t ws_bytes = 0;
     bool bound = false;
     // layout (byte offsets into ws)
-    size_t off_tw0 = 0, off_tw1 = 0, off_tw2 = 0, off_buf = 0, off_buf2 = 0, need = 0;
+    size_t off_tw0 = 0, off_tw1 = 0, off_tw2 = 0, off_tw3 = 0, off_buf = 0, off_buf2 = 0, need = 0;
     size_t off_hs = 0, off_beta = 0, off_grad = 0;  // 2D: prepared filter, beta, adjoint sums
     int64_t chunk = 0;           // transforms (1D four-step) or images (2D) per workspace chunk
     int fs_l1 = 0, fs_l2 = 0;    // four-step split
@@ -146,6 +146,8 @@ void layout(gbfft_plan *p) {
             off = align_up(off + (size_t)n2 * csize(p));
             p->off_tw2 = off;
             off = align_up(off + (size_t)n4s * csize(p));
+            p->off_tw3 = off;  // full inter-pass table of the cluster path
+            if (fft1d_cluster_supported(p->log2n, is_dbl(p))) off = align_up(off + (size_t)n * csize(p));
             p->off_buf = off;
             int64_t chunk = p->opt_chunk;
             if (chunk <= 0) {
@@ -236,6 +238,12 @@ int run_1d(gbfft_plan *p, const void *in, void *out, int dir, cudaStream_t s) {
     if (p->log2n <= max_single_log2(p)) {
         return launch(p, GBFFT_STAGE_FFT1D, s, [&] {
             return launch_fft1d(in, out, p->log2n, p->batch, dbl, dir, p->ws + p->off_tw0, scale, s);
+        });
+    }
+    if (p->opt_onchip && fft1d_cluster_supported(p->log2n, dbl)) {
+        return launch(p, GBFFT_STAGE_FFT1D_CLUSTER, s, [&] {
+            return launch_fft1d_cluster(in, out, p->log2n, p->batch, dir, p->ws + p->off_tw0, p->ws + p->off_tw1,
+                                        p->ws + p->off_tw3, scale, s);
         });
     }
     const size_t cs = csize(p);
@@ -391,7 +399,7 @@ int fft_plan_set_option(gbfft_plan_t p, int key, int64_t value) {
             drop_graph(p);
             return GBFFT_OK;
         case GBFFT_OPT_ONCHIP:
-            if (p->kind != KIND_2D || (value != 0 && value != 1)) return GBFFT_ERR_INVALID_VALUE;
+            if (p->kind == KIND_BATCH || (value != 0 && value != 1)) return GBFFT_ERR_INVALID_VALUE;
             p->opt_onchip = value;
             return GBFFT_OK;
         case GBFFT_OPT_ENABLE_BACKWARD:
@@ -427,6 +435,8 @@ int fft_plan_bind_workspace(gbfft_plan_t p, void *workspace, size_t bytes, gbfft
                 cudaError_t e = launch_twiddles(p->ws + p->off_tw0, 1 << p->fs_l1, dbl, s);
                 if (e == cudaSuccess) e = launch_twiddles(p->ws + p->off_tw1, 1 << p->fs_l2, dbl, s);
                 if (e == cudaSuccess) e = launch_fourstep_twiddles(p->ws + p->off_tw2, 1 << p->log2n, dbl, s);
+                if (e == cudaSuccess && fft1d_cluster_supported(p->log2n, dbl))
+                    e = launch_fourstep_full_twiddles(p->ws + p->off_tw3, 1 << p->log2n, p->fs_l2, s);
                 return e;
             });
         }
@@ -474,9 +484,12 @@ static cudaError_t ensure_aux(gbfft_plan *p) {
 // One chunk of the Sec. 5 pipeline: filter preparation on the side stream
 // while the forward row pass runs, then the fused column pass and the inverse
 // row pass.
+// crop_r, crop_c > 0: img and out are crop_r x crop_c images in the top-left
+// corner of the plan's zero-padded grid (Sec. 5 application path).
 static int pipeline_chunk(gbfft_plan *p, const float *img, const float *H, float *out, int nb, bool first,
-                          cudaStream_t s) {
+                          cudaStream_t s, int crop_r = 0, int crop_c = 0) {
     const int rows = 1 << p->log2r, cols = 1 << p->log2c;
+    const bool cropped = crop_r > 0;
     const int64_t half_px = (int64_t)rows * (cols / 2);
     const bool per_image = p->opt_h_stride != 0;
     RowsFwdArgs a;
@@ -493,7 +506,7 @@ static int pipeline_chunk(gbfft_plan *p, const float *img, const float *H, float
     a.scale = (float)(1.0 / ((double)rows * cols));
     a.tw = p->ws + p->off_tw0;
     const int terms = p->opt_precision ? (int)p->opt_precision + 1 : 0;  // split-BF16 tensor-core passes
-    if (!terms && p->opt_onchip && onchip_supported(rows, cols)) {
+    if (!terms && !cropped && p->opt_onchip && onchip_supported(rows, cols)) {
         return launch(p, GBFFT_STAGE_ONCHIP, s, [&] {
             return launch_onchip(img, H, out, p->opt_h_stride, rows, cols, nb, p->ws + p->off_tw0,
                                  p->ws + p->off_tw1, s);
@@ -524,6 +537,7 @@ static int pipeline_chunk(gbfft_plan *p, const float *img, const float *H, float
         if ((e = cudaEventRecord(p->ev_join, p->aux)) != cudaSuccess) return cuda_fail(e);
     }
     rc = launch(p, GBFFT_STAGE_ROWS_FWD, s, [&] {
+        if (cropped) return launch_rows_pad(true, img, a.spec, rows, cols, nb, crop_r, crop_c, a.tw, s);
         return terms ? launch_rows_tc(true, img, a.spec, rows, cols, nb, a.tw, terms, s) : launch_rows_fwd(a, s);
     });
     if (rc) return rc;
@@ -539,6 +553,7 @@ static int pipeline_chunk(gbfft_plan *p, const float *img, const float *H, float
     });
     if (rc) return rc;
     return launch(p, GBFFT_STAGE_ROWS_INV, s, [&] {
+        if (cropped) return launch_rows_pad(false, a.spec, out, rows, cols, nb, crop_r, crop_c, p->ws + p->off_tw0, s);
         return terms ? launch_rows_tc(false, a.spec, out, rows, cols, nb, p->ws + p->off_tw0, terms, s)
                      : launch_rows_inv(a.spec, out, rows, cols, nb, p->ws + p->off_tw0, s);
     });
@@ -556,6 +571,65 @@ int fft2_filter_ifft2(gbfft_plan_t p, const float *img, const float *H, float *o
         const int nb = (int)((p->batch - b0 < p->chunk) ? p->batch - b0 : p->chunk);
         rc = pipeline_chunk(p, img + b0 * np, H + b0 * p->opt_h_stride, out + b0 * np, nb, b0 == 0, s);
         if (rc) return rc;
+    }
+    return GBFFT_OK;
+}
+
+static bool misaligned4(const void *q) { return (reinterpret_cast<uintptr_t>(q) & 3) != 0; }
+
+int fft2_filter_ifft2_padded(gbfft_plan_t p, const float *img, int64_t in_rows, int64_t in_cols, const float *H,
+                             float *out, gbfft_stream_t stream) {
+    int rc = check_plan_ready(p);
+    if (rc) return rc;
+    if (p->kind != KIND_2D) return GBFFT_ERR_INVALID_VALUE;
+    if (!img || !H || !out) return GBFFT_ERR_NULL;
+    if (in_rows < 1 || in_cols < 1 || in_rows > (1 << p->log2r) || in_cols > (1 << p->log2c))
+        return GBFFT_ERR_INVALID_SIZE;
+    if (misaligned4(img) || misaligned4(out) || misaligned(H)) return GBFFT_ERR_MISALIGNED;
+    if (p->opt_precision != 0) return GBFFT_ERR_UNSUPPORTED;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t np = in_rows * in_cols;
+    for (int64_t b0 = 0; b0 < p->batch; b0 += p->chunk) {
+        const int nb = (int)((p->batch - b0 < p->chunk) ? p->batch - b0 : p->chunk);
+        rc = pipeline_chunk(p, img + b0 * np, H + b0 * p->opt_h_stride, out + b0 * np, nb, b0 == 0, s, (int)in_rows,
+                            (int)in_cols);
+        if (rc) return rc;
+    }
+    return GBFFT_OK;
+}
+
+int fft2_spectrum(gbfft_plan_t p, const float *img, int64_t in_rows, int64_t in_cols, float *mag,
+                  gbfft_stream_t stream) {
+    int rc = check_plan_ready(p);
+    if (rc) return rc;
+    if (p->kind != KIND_2D) return GBFFT_ERR_INVALID_VALUE;
+    if (!img || !mag) return GBFFT_ERR_NULL;
+    const int rows = 1 << p->log2r, cols = 1 << p->log2c;
+    if (in_rows < 1 || in_cols < 1 || in_rows > rows || in_cols > cols) return GBFFT_ERR_INVALID_SIZE;
+    if (misaligned4(img) || misaligned4(mag)) return GBFFT_ERR_MISALIGNED;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    // per-axis: F = DFT2 / (rows cols); Eq. 5: cols times that
+    const float scale = (float)(p->opt_scale_conv ? 1.0 / rows : 1.0 / ((double)rows * cols));
+    float *mag_T = reinterpret_cast<float *>(p->ws + p->off_hs);  // the prepared-filter area is scratch here
+    float *nyq = reinterpret_cast<float *>(p->ws + p->off_beta);
+    const int64_t np = in_rows * in_cols;
+    for (int64_t b0 = 0; b0 < p->batch; b0 += p->chunk) {
+        const int nb = (int)((p->batch - b0 < p->chunk) ? p->batch - b0 : p->chunk);
+        rc = launch(p, GBFFT_STAGE_ROWS_FWD, s, [&] {
+            return launch_rows_pad(true, img + b0 * np, p->ws + p->off_buf, rows, cols, nb, (int)in_rows,
+                                   (int)in_cols, p->ws + p->off_tw0, s);
+        });
+        if (rc) return rc;
+        for (int i = 0; i < nb; ++i) {
+            const char *spec = p->ws + p->off_buf + (size_t)i * (size_t)rows * (cols / 2) * 8;
+            rc = launch(p, GBFFT_STAGE_SPECTRUM, s, [&] {
+                cudaError_t e = launch_cols_spectrum(spec, mag_T, nyq, scale, rows, cols, p->ws + p->off_tw1, s);
+                if (e == cudaSuccess)
+                    e = launch_grad_scatter(mag_T, nyq, mag + (b0 + i) * (int64_t)rows * cols, rows, cols, s);
+                return e;
+            });
+            if (rc) return rc;
+        }
     }
     return GBFFT_OK;
 }
@@ -621,7 +695,9 @@ int fft2_filter_ifft2_backward(gbfft_plan_t p, const float *img, const float *H,
             if (rc) return rc;
         }
     }
-    return launch(p, GBFFT_STAGE_COLS_GRAD, s, [&] { return launch_grad_scatter(grad_T, grad_H, rows, cols, s); });
+    return launch(p, GBFFT_STAGE_COLS_GRAD, s, [&] {
+        return launch_grad_scatter(grad_T, grad_T + (size_t)(cols / 2) * rows, grad_H, rows, cols, s);
+    });
 }
 
 int fft2_batched_plan_create(int count, const int64_t *rows, const int64_t *cols, gbfft_plan_t *out) {

@@ -141,14 +141,15 @@ __global__ void __launch_bounds__(GradCfg<N>::THREADS)
 
 // grad_T [M/2 + 1][N] (slot order) -> grad_H [N][M] row-major, mirror bins filled.
 __global__ void __launch_bounds__(256)
-    k_grad_scatter(const float *__restrict__ grad_T, float *__restrict__ grad_H, int N, int M, int log2g) {
+    k_grad_scatter(const float *__restrict__ grad_T, const float *__restrict__ nyq, float *__restrict__ grad_H, int N,
+                   int M, int log2g) {
     __shared__ float tile[32][33];
     const int half = M >> 1;
     const int kb = blockIdx.x * 32, sb = blockIdx.y * 32;
     const int tx = threadIdx.x, ty = threadIdx.y;
     for (int i = ty; i < 32; i += 8) {
         const int k = kb + i, s = sb + tx;
-        tile[i][tx] = (k <= half && s < N) ? grad_T[(size_t)k * N + s] : 0.f;
+        tile[i][tx] = (k < half && s < N) ? grad_T[(size_t)k * N + s] : (k == half && s < N) ? nyq[s] : 0.f;
     }
     __syncthreads();
     for (int i = ty; i < 32; i += 8) {
@@ -199,11 +200,12 @@ cudaError_t launch_cols_grad(const void *spec_x, void *spec_g, const float *hs, 
     }
 }
 
-cudaError_t launch_grad_scatter(const float *grad_T, float *grad_H, int rows, int cols, cudaStream_t s) {
+cudaError_t launch_grad_scatter(const float *grad_T, const float *nyq, float *grad_H, int rows, int cols,
+                                cudaStream_t s) {
     int g = rows_pairs_per_block(cols);
     if (g > rows / 2) g = rows / 2;
     dim3 grid((cols / 2 + 1 + 31) / 32, (rows + 31) / 32);
-    k_grad_scatter<<<grid, dim3(32, 8), 0, s>>>(grad_T, grad_H, rows, cols, ilog2(g));
+    k_grad_scatter<<<grid, dim3(32, 8), 0, s>>>(grad_T, nyq, grad_H, rows, cols, ilog2(g));
     return cudaGetLastError();
 }
 

@@ -19,6 +19,9 @@
 namespace gbfft {
 
 template <int N, typename R> struct FsCfg {
+    // blocks per SM the register budget is sized for: 64 registers per thread
+    // hold an fp32 transform's 16 elements; fp64 needs twice as many
+    static constexpr int MINB = sizeof(R) == 4 ? 2 : 1;
     static constexpr int E = N < 16 ? N : 16;
     static constexpr int T = N / E;
     static constexpr int SMEM_ELEMS = (sizeof(R) == 4 ? 16384 : 8192);
@@ -44,7 +47,7 @@ __device__ __forceinline__ C tw_two_level(const C *__restrict__ t4, int idx, int
 
 // Pass A: column transforms of length N1 (= N) over the N1 x n2 view.
 template <int N, int DIR, typename R>
-__global__ void __launch_bounds__(512, 2)
+__global__ void __launch_bounds__(512, FsCfg<N, R>::MINB)
     k_fourstep_a(const typename cvec<R>::type *in, typename cvec<R>::type *tmp, int log2n2,
                  const typename cvec<R>::type *__restrict__ tw, const typename cvec<R>::type *__restrict__ t4,
                  int log2f) {
@@ -72,7 +75,7 @@ __global__ void __launch_bounds__(512, 2)
 
 // Pass B: row transforms of length N2 (= N) over the n1 x N2 view, stored at k1 + n1 k2.
 template <int N, int DIR, typename R>
-__global__ void __launch_bounds__(512, 2)
+__global__ void __launch_bounds__(512, FsCfg<N, R>::MINB)
     k_fourstep_b(const typename cvec<R>::type *tmp, typename cvec<R>::type *out, int log2n1,
                  const typename cvec<R>::type *__restrict__ tw, R scale) {
     typedef typename cvec<R>::type C;
@@ -102,7 +105,7 @@ static cudaError_t run_a(const void *in, void *tmp, int log2n2, long long nb, in
     constexpr int W = K::WMAX;  // <= 64 <= the other factor (>= 2^7)
     const size_t smem = (size_t)padded_len(N) * W * sizeof(C);
     auto kern = dir < 0 ? k_fourstep_a<N, -1, R> : k_fourstep_a<N, 1, R>;
-    cudaError_t e = set_smem_attrs((const void *)kern, smem, 2);
+    cudaError_t e = set_smem_attrs((const void *)kern, smem, K::MINB);
     if (e != cudaSuccess) return e;
     if (nb > 65535) return cudaErrorInvalidConfiguration;
     dim3 grid((1 << log2n2) / W, (unsigned)nb);
@@ -119,7 +122,7 @@ static cudaError_t run_b(const void *tmp, void *out, int log2n1, long long nb, i
     constexpr int W = K::WMAX;  // <= 64 <= the other factor (>= 2^7)
     const size_t smem = (size_t)padded_len(N) * W * sizeof(C);
     auto kern = dir < 0 ? k_fourstep_b<N, -1, R> : k_fourstep_b<N, 1, R>;
-    cudaError_t e = set_smem_attrs((const void *)kern, smem, 2);
+    cudaError_t e = set_smem_attrs((const void *)kern, smem, K::MINB);
     if (e != cudaSuccess) return e;
     if (nb > 65535) return cudaErrorInvalidConfiguration;
     dim3 grid((1 << log2n1) / W, (unsigned)nb);

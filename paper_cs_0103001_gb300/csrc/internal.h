@@ -24,6 +24,15 @@ cudaError_t launch_fourstep_twiddles(void *tw, int n, bool dbl, cudaStream_t s);
 
 // One-pass batched C2C transform, in-place allowed.  dir = -1 forward (Eq. E2
 // with `scale` = 1/n applied in the store), +1 inverse (scale 1).
+// One thread-block cluster per transform for complex64 lengths 2^15 .. 2^17:
+// the four-step split with its intermediate in distributed shared memory
+// (the four-step plan's tables of lengths n1 and n2, and the full inter-pass
+// table of launch_fourstep_full_twiddles).
+bool fft1d_cluster_supported(int log2n, bool dbl);
+cudaError_t launch_fft1d_cluster(const void *in, void *out, int log2n, long long batch, int dir, const void *tw_n1,
+                                 const void *tw_n2, const void *tw_full, double scale, cudaStream_t s);
+// complex64 table [n1][n2] of W_n^(k1 j2), each rounded once from FP64
+cudaError_t launch_fourstep_full_twiddles(void *tw, int n, int log2n2, cudaStream_t s);
 cudaError_t launch_fft1d(const void *in, void *out, int log2n, long long batch, bool dbl, int dir,
                          const void *tw, double scale, cudaStream_t s);
 
@@ -55,6 +64,16 @@ struct RowsFwdArgs {
     const void *tw;     // twiddles of length cols
 };
 int rows_pairs_per_block(int cols);
+// Row passes of zero-padded images: fwd reads nimg in_rows x in_cols images
+// (contiguous, pitch in_cols) as the top-left corner of rows x cols grids into
+// spec; !fwd writes that corner of the inverse back (Sec. 5 application path).
+cudaError_t launch_rows_pad(bool fwd, const void *src, void *dst, int rows, int cols, int nimg, int in_rows,
+                            int in_cols, const void *tw_cols, cudaStream_t s);
+// Spectrum display of one image from its row half spectra (slot order): the
+// column FFTs of spec (not modified), |F| * scale into mag_T [cols/2][rows] and
+// the Nyquist column into nyq [rows], both in slot order.
+cudaError_t launch_cols_spectrum(const void *spec, float *mag_T, float *nyq, float scale, int rows, int cols,
+                                 const void *tw_rows, cudaStream_t s);
 cudaError_t launch_rows_fwd(const RowsFwdArgs &a, cudaStream_t s);
 // Prepared filter alone (same values as RowsFwdArgs filter_mode 1/2) for nimg
 // filters H + i * h_stride into hs + i * hs_img, beta + i * beta_img.
@@ -82,7 +101,9 @@ cudaError_t launch_cols_tc(void *spec, const float *hs, const float *beta, long 
 cudaError_t launch_cols_grad(const void *spec_x, void *spec_g, const float *hs, const float *beta, float *grad_T,
                              int rows, int cols, int nimg, float scale, int accumulate, const void *tw_rows,
                              cudaStream_t s);
-// grad_T -> grad_H [rows][cols] row-major (both bins of every mirror pair).
-cudaError_t launch_grad_scatter(const float *grad_T, float *grad_H, int rows, int cols, cudaStream_t s);
+// grad_T [cols/2][rows] and the Nyquist column nyq [rows] (slot order) ->
+// grad_H [rows][cols] row-major (both bins of every mirror pair).
+cudaError_t launch_grad_scatter(const float *grad_T, const float *nyq, float *grad_H, int rows, int cols,
+                                cudaStream_t s);
 
 }  // namespace gbfft

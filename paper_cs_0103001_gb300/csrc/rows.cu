@@ -41,6 +41,29 @@ __global__ void __launch_bounds__(RowCfg<M>::THREADS, RowCfg<M>::THREADS <= 512 
     rows_inv_body<M>(spec + y * (M / 2) * N, out + y * N * M, N, log2g, tw, blockIdx.x, smraw);
 }
 
+// Row passes of a zero-padded image (Sec. 5 application path): image y of the
+// chunk is the crop.rows x crop.cols sub-image at img + y * img_stride; the
+// forward pass reads zeros outside it, the inverse pass writes only inside it.
+template <int M>
+__global__ void __launch_bounds__(RowCfg<M>::THREADS, RowCfg<M>::THREADS <= 512 ? 2 : 1)
+    k_rows_fwd_pad(const float *__restrict__ img, float2 *__restrict__ spec, int N, int log2g, Crop crop,
+                   long long img_stride, const float2 *__restrict__ tw) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const size_t y = blockIdx.y;
+    rows_fwd_body<M, Fp32Fft, true>(img + y * img_stride, spec + y * (M / 2) * N, nullptr, nullptr, nullptr, N,
+                                    log2g, false, 0.f, tw, blockIdx.x, smraw, Fp32Fft(), crop);
+}
+
+template <int M>
+__global__ void __launch_bounds__(RowCfg<M>::THREADS, RowCfg<M>::THREADS <= 512 ? 2 : 1)
+    k_rows_inv_pad(const float2 *__restrict__ spec, float *__restrict__ out, int N, int log2g, Crop crop,
+                   long long out_stride, const float2 *__restrict__ tw) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const size_t y = blockIdx.y;
+    rows_inv_body<M, Fp32Fft, true>(spec + y * (M / 2) * N, out + y * out_stride, N, log2g, tw, blockIdx.x, smraw,
+                                    Fp32Fft(), crop);
+}
+
 // Filter preparation on its own (the same values rows_fwd_body writes with
 // `prep`), as a tiled transpose: block (bx, by) of image z covers P mirror-row
 // pairs (a whole number of slot groups of G pairs) and K half-spectrum
@@ -137,6 +160,38 @@ static cudaError_t run_rows_inv(const void *spec, float *out, int rows, int nimg
     k_rows_inv<M><<<grid, K::THREADS, K::SMEM, s>>>(static_cast<const float2 *>(spec), out, rows, lg,
                                                     static_cast<const float2 *>(tw));
     return cudaGetLastError();
+}
+
+template <int M>
+static cudaError_t run_rows_pad(bool fwd, const void *src, void *dst, int rows, int nimg, int in_rows, int in_cols,
+                                const void *tw, cudaStream_t s) {
+    typedef RowCfg<M> K;
+    const void *kern = fwd ? (const void *)k_rows_fwd_pad<M> : (const void *)k_rows_inv_pad<M>;
+    cudaError_t e = set_smem<M>(kern);
+    if (e != cudaSuccess) return e;
+    const int lg = log2_pairs_per_block(rows, M);
+    dim3 grid((rows / 2) >> lg, nimg);
+    const Crop crop{in_rows, in_cols};
+    const long long stride = (long long)in_rows * in_cols;
+    if (fwd)
+        k_rows_fwd_pad<M><<<grid, K::THREADS, K::SMEM, s>>>(static_cast<const float *>(src), static_cast<float2 *>(dst),
+                                                             rows, lg, crop, stride, static_cast<const float2 *>(tw));
+    else
+        k_rows_inv_pad<M><<<grid, K::THREADS, K::SMEM, s>>>(static_cast<const float2 *>(src), static_cast<float *>(dst),
+                                                             rows, lg, crop, stride, static_cast<const float2 *>(tw));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rows_pad(bool fwd, const void *src, void *dst, int rows, int cols, int nimg, int in_rows,
+                            int in_cols, const void *tw_cols, cudaStream_t s) {
+    switch (ilog2(cols)) {
+#define GBFFT_CASE(L) \
+    case L: return run_rows_pad<(1 << L)>(fwd, src, dst, rows, nimg, in_rows, in_cols, tw_cols, s);
+        GBFFT_CASE(1) GBFFT_CASE(2) GBFFT_CASE(3) GBFFT_CASE(4) GBFFT_CASE(5) GBFFT_CASE(6) GBFFT_CASE(7)
+        GBFFT_CASE(8) GBFFT_CASE(9) GBFFT_CASE(10) GBFFT_CASE(11) GBFFT_CASE(12) GBFFT_CASE(13)
+#undef GBFFT_CASE
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_rows_fwd(const RowsFwdArgs &a, cudaStream_t s) {

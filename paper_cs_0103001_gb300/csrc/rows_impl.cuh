@@ -27,6 +27,13 @@
 
 namespace gbfft {
 
+// Sub-image of a zero-padded transform (Sec. 5 application path): the image
+// has `rows` x `cols` pixels (row pitch `cols`) in the top-left corner of the
+// N x M grid; the rest of the grid is zero on input and not written on output.
+struct Crop {
+    int rows, cols;
+};
+
 template <int M> struct RowCfg {
     static constexpr int E = M < 16 ? M : 16;
     static constexpr int T = M / E;
@@ -46,12 +53,14 @@ template <int M> struct RowCfg {
 // pairs from H (row-major [N][M]) into hs [M/2][N] and beta [N].  Every thread
 // of the block must call it; it ends after a block-wide barrier-free epilogue,
 // so a caller that reuses shared memory must synchronise first.
-template <int M, typename FFT = Fp32Fft>
+// With PAD, img is the crop.rows x crop.cols sub-image (pitch crop.cols) and
+// the rest of the grid reads as zero.
+template <int M, typename FFT = Fp32Fft, bool PAD = false>
 __device__ __forceinline__ void rows_fwd_body(const float *__restrict__ img, float2 *__restrict__ spec,
                                               const float *__restrict__ H, float *__restrict__ hs,
                                               float *__restrict__ beta, int N, int log2g, bool prep, float scale,
                                               const float2 *__restrict__ tw, int bx, unsigned char *smraw,
-                                              FFT fft = FFT()) {
+                                              FFT fft = FFT(), Crop crop = Crop{0, 0}) {
     typedef RowCfg<M> K;
     constexpr int E = K::E, T = K::T, SR = K::SR, H2 = M / 2;
     float2 *sm = reinterpret_cast<float2 *>(smraw);
@@ -64,7 +73,16 @@ __device__ __forceinline__ void rows_fwd_body(const float *__restrict__ img, flo
     rows_of_pair(active ? p : 0, N, a, b);
 
     float2 v[E];
-    if (active) {
+    if (PAD && active) {
+        const float *ra = img + (size_t)a * crop.cols;
+        const float *rb = img + (size_t)b * crop.cols;
+        const bool va = a < crop.rows, vb = b < crop.rows;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int x = t + T * e;
+            v[e] = make_float2(va && x < crop.cols ? __ldcs(ra + x) : 0.f, vb && x < crop.cols ? __ldcs(rb + x) : 0.f);
+        }
+    } else if (active) {
         const float *ra = img + (size_t)a * M;
         const float *rb = img + (size_t)b * M;
 #pragma unroll
@@ -155,10 +173,11 @@ __device__ __forceinline__ void rows_fwd_body(const float *__restrict__ img, flo
 
 // One block's share of the inverse row pass: spec [M/2][N] (slot order) of one
 // image -> rows of pairs bx*G .. bx*G + G - 1 of out [N][M], unscaled.
-template <int M, typename FFT = Fp32Fft>
+// With PAD, only the crop.rows x crop.cols sub-image is written (pitch crop.cols).
+template <int M, typename FFT = Fp32Fft, bool PAD = false>
 __device__ __forceinline__ void rows_inv_body(const float2 *__restrict__ spec, float *__restrict__ out, int N,
                                               int log2g, const float2 *__restrict__ tw, int bx,
-                                              unsigned char *smraw, FFT fft = FFT()) {
+                                              unsigned char *smraw, FFT fft = FFT(), Crop crop = Crop{0, 0}) {
     typedef RowCfg<M> K;
     constexpr int E = K::E, T = K::T, SR = K::SR, H2 = M / 2;
     float2 *sm = reinterpret_cast<float2 *>(smraw);
@@ -213,7 +232,18 @@ __device__ __forceinline__ void rows_inv_body(const float2 *__restrict__ spec, f
     // the exchange buffers overlap the staging area: the first exchange of
     // fft_regs starts with a block barrier, after every thread read its values
     fft.template run<M, E, 1>(v, sm + g * padded_len(M), tw, t);
-    if (active) {
+    if (PAD && active) {
+        float *ra = out + (size_t)a * crop.cols;
+        float *rb = out + (size_t)b * crop.cols;
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int x = t + T * e;
+            if (x < crop.cols) {
+                if (a < crop.rows) __stcs(ra + x, v[e].x);
+                if (b < crop.rows) __stcs(rb + x, v[e].y);
+            }
+        }
+    } else if (active) {
         float *ra = out + (size_t)a * M;
         float *rb = out + (size_t)b * M;
 #pragma unroll

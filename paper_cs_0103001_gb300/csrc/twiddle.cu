@@ -43,6 +43,23 @@ __global__ void k_fourstep_twiddles(C *tw, int n, int log2f) {
     tw[i] = C{(decltype(tw[0].x))c, (decltype(tw[0].x))s};
 }
 
+// Full inter-pass table of the split n = n1 n2: entry k1 * n2 + j2 holds
+// W_n^(k1 j2) (k1 j2 < n, so the phase needs no reduction).
+__global__ void k_fourstep_full_twiddles(float2 *tw, int n, int log2n2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const long long ph = (long long)(i >> log2n2) * (i & ((1 << log2n2) - 1));
+    double s, c;
+    sincospi(-2.0 * (double)ph / (double)n, &s, &c);
+    tw[i] = make_float2((float)c, (float)s);
+}
+
+cudaError_t launch_fourstep_full_twiddles(void *tw, int n, int log2n2, cudaStream_t s) {
+    const int threads = 256;
+    k_fourstep_full_twiddles<<<(n + threads - 1) / threads, threads, 0, s>>>(static_cast<float2 *>(tw), n, log2n2);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_twiddles(void *tw, int n, bool dbl, cudaStream_t s) {
     if (n < 2) return cudaSuccess;
     const int threads = 256;

@@ -107,3 +107,15 @@ def test_status_strings(nat):
     for code in range(-9, 1):
         assert nat.lib.gbfft_status_string(code)
     assert nat.lib.gbfft_version() >= 100
+
+
+def test_padded_and_spectrum_entry_checks(nat):
+    h = ctypes.c_void_p()
+    assert nat.lib.fft2_plan_create(512, 512, 1, 1, ctypes.byref(h)) == nat.OK
+    fake = ctypes.c_void_p(1 << 20)
+    assert nat.lib.fft2_filter_ifft2_padded(None, fake, 460, 506, fake, fake, None) == nat.ERR_NULL
+    assert nat.lib.fft2_spectrum(None, fake, 460, 506, fake, None) == nat.ERR_NULL
+    # no workspace bound yet
+    assert nat.lib.fft2_filter_ifft2_padded(h, fake, 460, 506, fake, fake, None) == nat.ERR_WORKSPACE
+    assert nat.lib.fft2_spectrum(h, fake, 460, 506, fake, None) == nat.ERR_WORKSPACE
+    assert nat.lib.fft_plan_destroy(h) == nat.OK
