@@ -81,6 +81,62 @@ __global__ void __launch_bounds__(256)
     const int p0 = blockIdx.x * P, k0 = blockIdx.y * K;
     const size_t z = blockIdx.z;
     const float *hb = H + z * h_stride;
+    const float hsc = 0.5f * scale;
+    // unit = (tile row r, four consecutive columns): row r = side * P + g is
+    // pair p0 + g's first or mirror row u; filter row u gives Hs[u][k] with the
+    // reversed run of row -u.
+    const int nq = K >> 2, units = (2 * P) << (log2k - 2);
+    for (int q = threadIdx.x; q < units; q += blockDim.x) {
+        const int r = q >> (log2k - 2), kq = (q & (nq - 1)) << 2;
+        const int side = r >> log2p, g = r & (P - 1);
+        int a, b;
+        rows_of_pair(p0 + g, N, a, b);
+        const int u = side ? b : a, mu = (N - u) & (N - 1);
+        const int ls = ((g >> log2g) << (log2g + 1)) + (side << log2g) + (g & (G - 1));
+        const int k = k0 + kq;
+        const float *Hu = hb + (size_t)u * M, *Hm = hb + (size_t)mu * M;
+        const float4 f = __ldcs(reinterpret_cast<const float4 *>(Hu + k));
+        // Hm[M - k - i], i = 0..3: the run [M-k-3, M-k] from two aligned quads
+        // (for k = 0 the element M - k is column 0 of the mirror row, read below)
+        const float4 m1 = __ldcs(reinterpret_cast<const float4 *>(Hm + (M - k - 4)));
+        const float m0 = k == 0 ? Hm[0] : __ldcs(Hm + (M - k));
+        float v0;
+        if (k == 0) {
+            const float h0 = 0.5f * (f.x + m0), h1 = 0.5f * (Hu[H2] + Hm[H2]);
+            v0 = hsc * (h0 + h1);
+            beta[z * beta_img + 2 * (size_t)p0 + ls] = hsc * (h0 - h1);
+        } else {
+            v0 = hsc * (f.x + m0);
+        }
+        float *tc = tile + kq * SR + ls;
+        tc[0] = v0;
+        tc[SR] = hsc * (f.y + m1.w);
+        tc[2 * SR] = hsc * (f.z + m1.z);
+        tc[3 * SR] = hsc * (f.w + m1.y);
+    }
+    __syncthreads();
+    // each column's 2P slots, four per store (2P >= 4 and every run starts 16-byte aligned)
+    float *hsb = hs + z * hs_img + 2 * (size_t)p0;
+    const int m = K << (log2p - 1);
+    for (int idx = threadIdx.x; idx < m; idx += blockDim.x) {
+        const int i = idx >> (log2p - 1), s = (idx & ((P >> 1) - 1)) << 2;
+        const float *tr = tile + i * SR + s;
+        *reinterpret_cast<float4 *>(hsb + (size_t)(k0 + i) * N + s) = make_float4(tr[0], tr[1], tr[2], tr[3]);
+    }
+}
+
+// Scalar form of the same tile for spectra narrower than four columns (cols < 8)
+// or images of fewer than four rows.
+__global__ void __launch_bounds__(256)
+    k_filter_prep_small(const float *__restrict__ H, float *__restrict__ hs, float *__restrict__ beta, int N, int M,
+                  int log2g, int log2p, int log2k, float scale, long long h_stride, long long hs_img,
+                  long long beta_img) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    float *tile = reinterpret_cast<float *>(smraw);
+    const int G = 1 << log2g, P = 1 << log2p, K = 1 << log2k, H2 = M >> 1, SR = 2 * P + 1;
+    const int p0 = blockIdx.x * P, k0 = blockIdx.y * K;
+    const size_t z = blockIdx.z;
+    const float *hb = H + z * h_stride;
     // rows of the tile: r = side * P + g, pair p0 + g; local slot of that row
     const int n = (2 * P) << log2k;
     for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
@@ -119,11 +175,17 @@ cudaError_t launch_filter_prep(const float *H, float *hs, float *beta, int rows,
     if (pp > rows / 2) pp = rows / 2;
     int kk = cols / 2 < 32 ? cols / 2 : 32;
     const size_t smem = (size_t)kk * (2 * pp + 1) * sizeof(float);
-    cudaError_t e = set_smem_attrs((const void *)k_filter_prep, smem);
+    const bool quads = kk >= 4 && pp >= 2;  // four columns per load, four slots per store
+    const void *kern = quads ? (const void *)k_filter_prep : (const void *)k_filter_prep_small;
+    cudaError_t e = set_smem_attrs(kern, smem);
     if (e != cudaSuccess) return e;
     dim3 grid((rows / 2) / pp, (cols / 2) / kk, nimg);
-    k_filter_prep<<<grid, 256, smem, s>>>(H, hs, beta, rows, cols, ilog2(g), ilog2(pp), ilog2(kk), scale, h_stride,
-                                          hs_img, beta_img);
+    if (quads)
+        k_filter_prep<<<grid, 256, smem, s>>>(H, hs, beta, rows, cols, ilog2(g), ilog2(pp), ilog2(kk), scale, h_stride,
+                                              hs_img, beta_img);
+    else
+        k_filter_prep_small<<<grid, 256, smem, s>>>(H, hs, beta, rows, cols, ilog2(g), ilog2(pp), ilog2(kk), scale,
+                                                    h_stride, hs_img, beta_img);
     return cudaGetLastError();
 }
 
