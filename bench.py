@@ -304,6 +304,28 @@ def run_gbfft(args):
     torch.cuda.synchronize(dev)
     e2e_ms = max_over_ranks(e0.elapsed_time(e1) / e_steps, world, dev)
 
+    # the host link's own ceiling for the same bytes: the step's two copies
+    # alone, concurrently on their streams (no compute)
+    def copies_only(n):
+        for i in range(n):
+            j = i & 1
+            with torch.cuda.stream(s_in):
+                img_d[j].copy_(img_h, non_blocking=True)
+            with torch.cuda.stream(s_out):
+                out_h[j].copy_(out_d[j], non_blocking=True)
+
+    copies_only(3)
+    torch.cuda.synchronize(dev)
+    c0 = torch.cuda.Event(enable_timing=True)
+    c1 = torch.cuda.Event(enable_timing=True)
+    c0.record(s_in)
+    s_out.wait_event(c0)
+    copies_only(e_steps)
+    s_in.wait_stream(s_out)
+    c1.record(s_in)
+    torch.cuda.synchronize(dev)
+    copy_ms = c0.elapsed_time(c1) / e_steps
+
     result = None
     if rank == 0:
         peak, peak_kind = measured_peaks()
@@ -362,9 +384,10 @@ def run_gbfft(args):
                              "seconds": round(cpu_s, 3)},
             "e2e": {"value": round(world * METRIC_BYTES_PER_PX * px / (e2e_ms * 1e-3) / 1e9, 1), "unit": "GB/s",
                     "ms_per_step": round(e2e_ms, 4), "h2d_bytes_per_step": 4 * px, "d2h_bytes_per_step": 4 * px,
-                    "steps": e_steps,
+                    "steps": e_steps, "copies_only_ms_per_step": round(copy_ms, 4),
                     "note": "pinned host image in, filtered image out, every step; filter resident; "
-                            "copies overlapped with compute on three streams"},
+                            "copies overlapped with compute on three streams; copies_only = the same two "
+                            "copies per step with no compute (the host link's ceiling)"},
             "gpu_launches": int(round(launches_per_step * args.steps)),
             "variants": dict(run_variants(), pipeline4096_precision=_guard(lambda: variant_precision(img, H, ref, flush)))
             if args.variants else None,

@@ -16,16 +16,23 @@
 #include "fft_core.cuh"
 #include "internal.h"
 
+#ifndef GBFFT_FS_BIGN
+#define GBFFT_FS_BIGN 4096  // fp32 factor lengths from which a block has 1024 threads
+#endif
+
 namespace gbfft {
 
 template <int N, typename R> struct FsCfg {
     // blocks per SM the register budget is sized for: 64 registers per thread
     // hold an fp32 transform's 16 elements; fp64 needs twice as many
-    static constexpr int MINB = sizeof(R) == 4 ? 2 : 1;
+    // threads per block at most: 1024 for long fp32 factors, so that a tile
+    // spans at least four columns (32-byte runs); 512 otherwise (two blocks per SM)
+    static constexpr int MAXT = sizeof(R) == 4 && N >= GBFFT_FS_BIGN ? 1024 : 512;
+    static constexpr int MINB = sizeof(R) == 4 && MAXT <= 512 ? 2 : 1;
     static constexpr int E = N < 16 ? N : 16;
     static constexpr int T = N / E;
     static constexpr int SMEM_ELEMS = (sizeof(R) == 4 ? 16384 : 8192);
-    static constexpr int W0 = SMEM_ELEMS / N < 512 / T ? SMEM_ELEMS / N : 512 / T;
+    static constexpr int W0 = SMEM_ELEMS / N < MAXT / T ? SMEM_ELEMS / N : MAXT / T;
     static constexpr int WMAX = W0 > 64 ? 64 : (W0 < 1 ? 1 : W0);
 };
 
@@ -47,7 +54,7 @@ __device__ __forceinline__ C tw_two_level(const C *__restrict__ t4, int idx, int
 
 // Pass A: column transforms of length N1 (= N) over the N1 x n2 view.
 template <int N, int DIR, typename R>
-__global__ void __launch_bounds__(512, FsCfg<N, R>::MINB)
+__global__ void __launch_bounds__(FsCfg<N, R>::MAXT, FsCfg<N, R>::MINB)
     k_fourstep_a(const typename cvec<R>::type *in, typename cvec<R>::type *tmp, int log2n2,
                  const typename cvec<R>::type *__restrict__ tw, const typename cvec<R>::type *__restrict__ t4,
                  int log2f) {
@@ -75,7 +82,7 @@ __global__ void __launch_bounds__(512, FsCfg<N, R>::MINB)
 
 // Pass B: row transforms of length N2 (= N) over the n1 x N2 view, stored at k1 + n1 k2.
 template <int N, int DIR, typename R>
-__global__ void __launch_bounds__(512, FsCfg<N, R>::MINB)
+__global__ void __launch_bounds__(FsCfg<N, R>::MAXT, FsCfg<N, R>::MINB)
     k_fourstep_b(const typename cvec<R>::type *tmp, typename cvec<R>::type *out, int log2n1,
                  const typename cvec<R>::type *__restrict__ tw, R scale) {
     typedef typename cvec<R>::type C;

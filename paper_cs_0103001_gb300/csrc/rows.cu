@@ -3,6 +3,10 @@
 #include "internal.h"
 #include "rows_impl.cuh"
 
+#ifndef GBFFT_PREP_K
+#define GBFFT_PREP_K 64  // half-spectrum columns per filter-preparation tile
+#endif
+
 namespace gbfft {
 
 int rows_pairs_per_block(int cols) {
@@ -86,6 +90,7 @@ __global__ void __launch_bounds__(256)
     // pair p0 + g's first or mirror row u; filter row u gives Hs[u][k] with the
     // reversed run of row -u.
     const int nq = K >> 2, units = (2 * P) << (log2k - 2);
+#pragma unroll 2
     for (int q = threadIdx.x; q < units; q += blockDim.x) {
         const int r = q >> (log2k - 2), kq = (q & (nq - 1)) << 2;
         const int side = r >> log2p, g = r & (P - 1);
@@ -173,7 +178,7 @@ cudaError_t launch_filter_prep(const float *H, float *hs, float *beta, int rows,
     if (g > rows / 2) g = rows / 2;
     int pp = g > 16 ? g : 16;  // pairs per tile: whole slot groups, runs of >= 32 slots
     if (pp > rows / 2) pp = rows / 2;
-    int kk = cols / 2 < 32 ? cols / 2 : 32;
+    int kk = cols / 2 < GBFFT_PREP_K ? cols / 2 : GBFFT_PREP_K;
     const size_t smem = (size_t)kk * (2 * pp + 1) * sizeof(float);
     const bool quads = kk >= 4 && pp >= 2;  // four columns per load, four slots per store
     const void *kern = quads ? (const void *)k_filter_prep : (const void *)k_filter_prep_small;
