@@ -89,7 +89,8 @@ typedef enum {
      * adjoint is always computed with FP32 butterflies. */
     GBFFT_OPT_PRECISION = 3,
     /* 2D: number of images whose spectra share the workspace at a time
-     * (0 = choose from the L2 size).  Changes fft_plan_workspace_bytes. */
+     * (0 = as many as 1 GiB of half spectra holds, at most the batch).
+     * Changes fft_plan_workspace_bytes. */
     GBFFT_OPT_IMAGES_PER_CHUNK = 4,
     /* 1 = record a CUDA event pair around every kernel launch of this plan
      * (read with gbfft_plan_profile_read) and run every kernel on the

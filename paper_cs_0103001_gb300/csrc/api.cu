@@ -82,15 +82,6 @@ size_t csize(const gbfft_plan *p) { return is_dbl(p) ? 16 : 8; }
 
 int max_single_log2(const gbfft_plan *p) { return is_dbl(p) ? kMaxSinglePassLog2F64 : kMaxSinglePassLog2F32; }
 
-int64_t l2_budget_bytes() {
-    int dev = 0, l2 = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, dev) == cudaSuccess &&
-        l2 > 0)
-        return (int64_t)l2 * 3 / 8;
-    cudaGetLastError();
-    return 48ll << 20;
-}
-
 void layout_batched(gbfft_plan *p) {
     size_t off = 0;
     p->off_bimgs = off;
@@ -151,7 +142,9 @@ void layout(gbfft_plan *p) {
             p->off_buf = off;
             int64_t chunk = p->opt_chunk;
             if (chunk <= 0) {
-                chunk = l2_budget_bytes() / (n * (int64_t)csize(p));
+                // a large chunk: one launch of many blocks per pass costs less than
+                // keeping the intermediate in L2 gains (the passes are not HBM-bound)
+                chunk = kFourStepChunkBytes / (n * (int64_t)csize(p));
                 if (chunk < 1) chunk = 1;
             }
             if (chunk > p->batch) chunk = p->batch;
@@ -169,7 +162,9 @@ void layout(gbfft_plan *p) {
         const int64_t img_bytes = half_px * 8;
         int64_t chunk = p->opt_chunk;
         if (chunk <= 0) {
-            chunk = l2_budget_bytes() / img_bytes;
+            // many images per launch: the kernels are bound by the SM, not by HBM,
+            // so fewer, larger launches beat an L2-sized spectrum buffer
+            chunk = kPipelineChunkBytes / img_bytes;
             if (chunk < 1) chunk = 1;
         }
         if (chunk > p->batch) chunk = p->batch;

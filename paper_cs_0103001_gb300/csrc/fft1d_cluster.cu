@@ -24,17 +24,28 @@
 
 namespace cg = cooperative_groups;
 
+#ifndef GBFFT_CL_PTS
+#define GBFFT_CL_PTS 8192  // points per CTA
+#endif
+#ifndef GBFFT_CL_CMAX
+#define GBFFT_CL_CMAX 8  // largest cluster (8 is the portable limit)
+#endif
+#ifndef GBFFT_CL_MINB4K
+#define GBFFT_CL_MINB4K 3  // CTAs per SM the registers are sized for at 4096 points per CTA
+#endif
+
 namespace gbfft {
 
 template <int L> struct ClCfg {
     static constexpr int N = 1 << L;
     static constexpr int N1 = 1 << (L / 2), N2 = 1 << (L - L / 2);
-    // CTAs per cluster: 8192 points each up to the portable cluster size of 8;
-    // 256 threads, so that two CTAs fit an SM and one's memory phases overlap
-    // the other's transforms
-    static constexpr int C = N / 8192 < 8 ? N / 8192 : 8;
+    // CTAs per cluster: GBFFT_CL_PTS points each, up to the cluster size limit;
+    // 256 threads, so that several CTAs fit an SM and one's memory phases
+    // overlap another's transforms
+    static constexpr int CMAX = GBFFT_CL_CMAX;
+    static constexpr int C = N / GBFFT_CL_PTS < CMAX ? N / GBFFT_CL_PTS : CMAX;
     static constexpr int THREADS = 256, E = 16;      // 4096 points per round
-    static constexpr int MINB = N / C <= 8192 ? 2 : 1;
+    static constexpr int MINB = N / C <= 4096 ? GBFFT_CL_MINB4K : (N / C <= 8192 ? 2 : 1);
     static constexpr int T1 = N1 / E, WA = THREADS / T1;  // step A: columns per round
     static constexpr int T2 = N2 / E, WB = THREADS / T2;  // step B: rows per round
     static constexpr int CJ = N2 / C, CK = N1 / C;   // columns (A) and rows (B) per CTA
@@ -43,7 +54,7 @@ template <int L> struct ClCfg {
     static constexpr int EXA = padded_len(N1) * WA, EXB = padded_len(N2) * WB;
     static constexpr int EXCH = EXA > EXB ? EXA : EXB;
     static constexpr size_t SMEM = (size_t)(TILE + EXCH) * sizeof(float2);
-    static_assert(C >= 2 && C <= 8, "cluster size");
+    static_assert(C >= 2 && C <= 16, "cluster size");
     static_assert(CJ % WA == 0 && CK % WB == 0, "whole rounds");
     static_assert(SMEM <= 227 * 1024, "shared memory");
 };
@@ -122,6 +133,8 @@ static cudaError_t run_cluster(const void *in, void *out, long long batch, int d
     typedef ClCfg<L> K;
     auto kern = dir < 0 ? k_fft1d_cluster<L, -1> : k_fft1d_cluster<L, 1>;
     cudaError_t e = set_smem_attrs((const void *)kern, K::SMEM, K::MINB);
+    if (e == cudaSuccess && K::C > 8)
+        e = cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
     for (long long b0 = 0; b0 < batch; b0 += 65535) {
         const unsigned nb = (unsigned)(batch - b0 < 65535 ? batch - b0 : 65535);

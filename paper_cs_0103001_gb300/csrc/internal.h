@@ -11,6 +11,8 @@ namespace gbfft {
 // thread block); longer transforms use the two-pass four-step schedule.
 constexpr int kMaxSinglePassLog2F32 = 14;  // 16384 complex64 = 128 KiB + pad
 constexpr int kMaxSinglePassLog2F64 = 13;  // 8192 complex128 = 128 KiB + pad
+constexpr long long kFourStepChunkBytes = 512ll << 20;  // 1D four-step intermediate per chunk
+constexpr long long kPipelineChunkBytes = 1ll << 30;     // 2D half spectra per chunk
 constexpr int kMaxLog2 = 24;
 constexpr int kMax2DLog2 = 13;
 
