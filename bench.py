@@ -453,7 +453,7 @@ def variant_fft1d(log2n: int, dtype: str = "c64", steps: int = 10):
 
 def variant_batched(count: int = 512, steps: int = 5):
     """Uneven batch: `count` skies, sides in {64..2048}, own Gaussian filter
-    each, three persistent launches replayed from a CUDA graph."""
+    each, four persistent launches replayed from a CUDA graph."""
     import torch
 
     import paper_cs_0103001_gb300 as gb

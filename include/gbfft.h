@@ -103,7 +103,8 @@ typedef enum {
     GBFFT_OPT_ENABLE_BACKWARD = 6,
     /* Batched plans: thread blocks per SM of each persistent stage launch
      * (0 = as many as fit, the default; fft_plan_autotune sets it per stage).
-     * fft_plan_get_option returns the three stages packed 8 bits each. */
+     * fft_plan_get_option returns the four stages packed 8 bits each, from
+     * the low byte: forward rows, columns, inverse rows, filter preparation. */
     GBFFT_OPT_BLOCKS_PER_SM = 7,
     /* Batched plans: 1 (default) = capture the three stage launches in a CUDA
      * graph on the first call and replay it while the image-pointer array and

@@ -148,7 +148,7 @@ class Plan2D(_PlanBase):
 
 class Plan2DBatched(_PlanBase):
     """Sec. 5 pipeline over images of uneven power-of-two sizes (16..4096 per
-    side), each with its own filter, in three persistent launches (optionally
+    side), each with its own filter, in four persistent launches (optionally
     replayed from a CUDA graph).  `shapes` is a list of (rows, cols)."""
 
     def __init__(self, shapes, device, options=None):

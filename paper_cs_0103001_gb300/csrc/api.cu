@@ -57,18 +57,18 @@ struct gbfft_plan {
     std::vector<ProfRec> prof;
     // batched plans (KIND_BATCH)
     std::vector<BatchImage> bimgs;
-    std::vector<BatchItem> bitems[3];
+    std::vector<BatchItem> bitems[kBatchStages];
     std::map<int, size_t> tw_off;  // twiddle table per distinct length
-    size_t off_bimgs = 0, off_bitems[3] = {0, 0, 0};
-    size_t bsmem[3] = {0, 0, 0};
-    int64_t opt_bps[3] = {0, 0, 0};  // blocks per SM per stage (0 = as many as fit)
+    size_t off_bimgs = 0, off_bitems[kBatchStages] = {0, 0, 0, 0};
+    size_t bsmem[kBatchStages] = {0, 0, 0, 0};
+    int64_t opt_bps[kBatchStages] = {0, 0, 0, 0};  // blocks per SM per stage (0 = as many as fit)
     int64_t opt_graph = 1;
     int64_t opt_onchip = 1;
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
     const void *graph_ptrs = nullptr;
-    int graph_grid[3] = {0, 0, 0};
+    int graph_grid[kBatchStages] = {0, 0, 0, 0};
     // 2D: side stream for the filter preparation, forked from / joined to the
     // caller's stream with events
     cudaStream_t aux = nullptr;
@@ -86,7 +86,7 @@ void layout_batched(gbfft_plan *p) {
     size_t off = 0;
     p->off_bimgs = off;
     off = align_up(off + p->bimgs.size() * sizeof(BatchImage));
-    for (int st = 0; st < 3; ++st) {
+    for (int st = 0; st < kBatchStages; ++st) {
         p->off_bitems[st] = off;
         off = align_up(off + p->bitems[st].size() * sizeof(BatchItem));
     }
@@ -279,7 +279,7 @@ int batched_grid(gbfft_plan *p, int st, cudaError_t *err) {
 
 cudaError_t batched_launch_all(gbfft_plan *p, const gbfft_image_ptrs *ptrs, cudaStream_t s, const int *grid) {
     const BatchImage *imgs = reinterpret_cast<const BatchImage *>(p->ws + p->off_bimgs);
-    for (int st = 0; st < 3; ++st) {
+    for (int st : kBatchOrder) {
         const BatchItem *items = reinterpret_cast<const BatchItem *>(p->ws + p->off_bitems[st]);
         cudaError_t e = launch_batched_stage(st, grid[st], p->bsmem[st], imgs, items, (int)p->bitems[st].size(), ptrs,
                                              p->ws, s);
@@ -385,7 +385,7 @@ int fft_plan_set_option(gbfft_plan_t p, int key, int64_t value) {
             return GBFFT_OK;
         case GBFFT_OPT_BLOCKS_PER_SM:
             if (p->kind != KIND_BATCH || value < 0 || value > 64) return GBFFT_ERR_INVALID_VALUE;
-            p->opt_bps[0] = p->opt_bps[1] = p->opt_bps[2] = value;
+            for (int st = 0; st < kBatchStages; ++st) p->opt_bps[st] = value;
             drop_graph(p);
             return GBFFT_OK;
         case GBFFT_OPT_USE_GRAPH:
@@ -447,7 +447,7 @@ int fft_plan_bind_workspace(gbfft_plan_t p, void *workspace, size_t bytes, gbfft
             // tables live in plan-owned host vectors, so the copies may complete later
             cudaError_t e = cudaMemcpyAsync(p->ws + p->off_bimgs, p->bimgs.data(),
                                             p->bimgs.size() * sizeof(BatchImage), cudaMemcpyHostToDevice, s);
-            for (int st = 0; st < 3 && e == cudaSuccess; ++st)
+            for (int st = 0; st < kBatchStages && e == cudaSuccess; ++st)
                 e = cudaMemcpyAsync(p->ws + p->off_bitems[st], p->bitems[st].data(),
                                     p->bitems[st].size() * sizeof(BatchItem), cudaMemcpyHostToDevice, s);
             for (const auto &kv : p->tw_off)
@@ -487,19 +487,11 @@ static int pipeline_chunk(gbfft_plan *p, const float *img, const float *H, float
     const bool cropped = crop_r > 0;
     const int64_t half_px = (int64_t)rows * (cols / 2);
     const bool per_image = p->opt_h_stride != 0;
-    RowsFwdArgs a;
-    a.img = img;
-    a.spec = p->ws + p->off_buf;
-    a.rows = rows;
-    a.cols = cols;
-    a.nimg = nb;
-    a.H = H;
-    a.hs = reinterpret_cast<float *>(p->ws + p->off_hs);
-    a.beta = reinterpret_cast<float *>(p->ws + p->off_beta);
-    a.h_stride = p->opt_h_stride;
-    a.filter_mode = 0;  // prepared separately below
-    a.scale = (float)(1.0 / ((double)rows * cols));
-    a.tw = p->ws + p->off_tw0;
+    void *spec = p->ws + p->off_buf;
+    float *hs = reinterpret_cast<float *>(p->ws + p->off_hs);
+    float *beta = reinterpret_cast<float *>(p->ws + p->off_beta);
+    const float scale = (float)(1.0 / ((double)rows * cols));
+    const void *tw = p->ws + p->off_tw0;
     const int terms = p->opt_precision ? (int)p->opt_precision + 1 : 0;  // split-BF16 tensor-core passes
     if (!terms && !cropped && p->opt_onchip && onchip_supported(rows, cols)) {
         return launch(p, GBFFT_STAGE_ONCHIP, s, [&] {
@@ -514,7 +506,7 @@ static int pipeline_chunk(gbfft_plan *p, const float *img, const float *H, float
     int rc;
     if (prep && !side) {
         rc = launch(p, GBFFT_STAGE_FILTER_PREP, s, [&] {
-            return launch_filter_prep(H, a.hs, a.beta, rows, cols, per_image ? nb : 1, a.scale, p->opt_h_stride,
+            return launch_filter_prep(H, hs, beta, rows, cols, per_image ? nb : 1, scale, p->opt_h_stride,
                                       per_image ? half_px : 0, per_image ? rows : 0, s);
         });
         if (rc) return rc;
@@ -525,15 +517,16 @@ static int pipeline_chunk(gbfft_plan *p, const float *img, const float *H, float
         if (e == cudaSuccess) e = cudaStreamWaitEvent(p->aux, p->ev_fork, 0);
         if (e != cudaSuccess) return cuda_fail(e);
         rc = launch(p, GBFFT_STAGE_FILTER_PREP, p->aux, [&] {
-            return launch_filter_prep(H, a.hs, a.beta, rows, cols, per_image ? nb : 1, a.scale, p->opt_h_stride,
+            return launch_filter_prep(H, hs, beta, rows, cols, per_image ? nb : 1, scale, p->opt_h_stride,
                                       per_image ? half_px : 0, per_image ? rows : 0, p->aux);
         });
         if (rc) return rc;
         if ((e = cudaEventRecord(p->ev_join, p->aux)) != cudaSuccess) return cuda_fail(e);
     }
     rc = launch(p, GBFFT_STAGE_ROWS_FWD, s, [&] {
-        if (cropped) return launch_rows_pad(true, img, a.spec, rows, cols, nb, crop_r, crop_c, a.tw, s);
-        return terms ? launch_rows_tc(true, img, a.spec, rows, cols, nb, a.tw, terms, s) : launch_rows_fwd(a, s);
+        if (cropped) return launch_rows_pad(true, img, spec, rows, cols, nb, crop_r, crop_c, tw, s);
+        return terms ? launch_rows_tc(true, img, spec, rows, cols, nb, tw, terms, s)
+                     : launch_rows_fwd(img, spec, rows, cols, nb, tw, s);
     });
     if (rc) return rc;
     if (side) {
@@ -542,15 +535,14 @@ static int pipeline_chunk(gbfft_plan *p, const float *img, const float *H, float
     }
     const long long hs_img = per_image ? half_px : 0, beta_img = per_image ? rows : 0;
     rc = launch(p, GBFFT_STAGE_COLS, s, [&] {
-        return terms ? launch_cols_tc(a.spec, a.hs, a.beta, hs_img, beta_img, rows, cols, nb, p->ws + p->off_tw1, terms,
-                                      s)
-                     : launch_cols_filter(a.spec, a.hs, a.beta, hs_img, beta_img, rows, cols, nb, p->ws + p->off_tw1, s);
+        return terms ? launch_cols_tc(spec, hs, beta, hs_img, beta_img, rows, cols, nb, p->ws + p->off_tw1, terms, s)
+                     : launch_cols_filter(spec, hs, beta, hs_img, beta_img, rows, cols, nb, p->ws + p->off_tw1, s);
     });
     if (rc) return rc;
     return launch(p, GBFFT_STAGE_ROWS_INV, s, [&] {
-        if (cropped) return launch_rows_pad(false, a.spec, out, rows, cols, nb, crop_r, crop_c, p->ws + p->off_tw0, s);
-        return terms ? launch_rows_tc(false, a.spec, out, rows, cols, nb, p->ws + p->off_tw0, terms, s)
-                     : launch_rows_inv(a.spec, out, rows, cols, nb, p->ws + p->off_tw0, s);
+        if (cropped) return launch_rows_pad(false, spec, out, rows, cols, nb, crop_r, crop_c, tw, s);
+        return terms ? launch_rows_tc(false, spec, out, rows, cols, nb, tw, terms, s)
+                     : launch_rows_inv(spec, out, rows, cols, nb, tw, s);
     });
 }
 
@@ -658,25 +650,19 @@ int fft2_filter_ifft2_backward(gbfft_plan_t p, const float *img, const float *H,
     const float scale = (float)(1.0 / (double)np);
     for (int64_t b0 = 0; b0 < p->batch; b0 += p->chunk) {
         const int nb = (int)((p->batch - b0 < p->chunk) ? p->batch - b0 : p->chunk);
-        RowsFwdArgs a;
-        a.img = img + b0 * np;
-        a.spec = spec_x;
-        a.rows = rows;
-        a.cols = cols;
-        a.nimg = nb;
-        a.H = H;
-        a.hs = hs;
-        a.beta = beta;
-        a.h_stride = 0;
-        a.filter_mode = b0 == 0 ? 1 : 0;
-        a.scale = scale;
-        a.tw = p->ws + p->off_tw0;
-        rc = launch(p, GBFFT_STAGE_ROWS_FWD, s, [&] { return launch_rows_fwd(a, s); });
+        if (b0 == 0) {  // the shared filter, prepared once
+            rc = launch(p, GBFFT_STAGE_FILTER_PREP, s, [&] {
+                return launch_filter_prep(H, hs, beta, rows, cols, 1, scale, 0, 0, 0, s);
+            });
+            if (rc) return rc;
+        }
+        rc = launch(p, GBFFT_STAGE_ROWS_FWD, s, [&] {
+            return launch_rows_fwd(img + b0 * np, spec_x, rows, cols, nb, p->ws + p->off_tw0, s);
+        });
         if (rc) return rc;
-        a.img = grad_out + b0 * np;
-        a.spec = spec_g;
-        a.filter_mode = 0;
-        rc = launch(p, GBFFT_STAGE_ROWS_FWD, s, [&] { return launch_rows_fwd(a, s); });
+        rc = launch(p, GBFFT_STAGE_ROWS_FWD, s, [&] {
+            return launch_rows_fwd(grad_out + b0 * np, spec_g, rows, cols, nb, p->ws + p->off_tw0, s);
+        });
         if (rc) return rc;
         rc = launch(p, GBFFT_STAGE_COLS_GRAD, s, [&] {
             return launch_cols_grad(spec_x, spec_g, hs, beta, grad_T, rows, cols, nb, scale, b0 > 0 ? 1 : 0,
@@ -709,7 +695,7 @@ int fft2_batched_plan_create(int count, const int64_t *rows, const int64_t *cols
         double cost;
         BatchItem it;
     };
-    std::vector<Costed> work[3];
+    std::vector<Costed> work[kBatchStages];
     for (int i = 0; i < count; ++i) {
         const int lr = ilog2_exact(rows[i]), lc = ilog2_exact(cols[i]);
         if (lr < kBatchMinLog2 || lr > kBatchMaxLog2 || lc < kBatchMinLog2 || lc > kBatchMaxLog2) {
@@ -736,11 +722,15 @@ int fft2_batched_plan_create(int count, const int64_t *rows, const int64_t *cols
         const int ncol = (im.cols / 2 + w - 1) / w;
         const double ccol = 2.0 * w * im.rows * lr;
         for (int bx = 0; bx < ncol; ++bx) work[1].push_back({ccol, {i, bx}});
+        const int nprep = batch_prep_tiles(im.rows, im.cols);
+        const double cprep = (double)im.rows * im.cols / 2 / nprep;
+        for (int bx = 0; bx < nprep; ++bx) work[3].push_back({cprep, {i, bx}});
         p->bsmem[0] = std::max(p->bsmem[0], batch_row_smem(im.cols));
         p->bsmem[1] = std::max(p->bsmem[1], batch_col_smem(im.rows));
+        p->bsmem[3] = std::max(p->bsmem[3], batch_prep_smem(im.rows, im.cols));
     }
     p->bsmem[2] = p->bsmem[0];
-    for (int st = 0; st < 3; ++st) {
+    for (int st = 0; st < kBatchStages; ++st) {
         // largest first; equal costs keep image order
         std::stable_sort(work[st].begin(), work[st].end(),
                          [](const Costed &a, const Costed &b) { return a.cost > b.cost; });
@@ -758,15 +748,18 @@ int fft2_filter_ifft2_batched(gbfft_plan_t p, const gbfft_image_ptrs *images, gb
     if (!images) return GBFFT_ERR_NULL;
     if (misaligned(images)) return GBFFT_ERR_MISALIGNED;
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-    int grid[3];
+    int grid[kBatchStages];
     cudaError_t e = cudaSuccess;
-    for (int st = 0; st < 3; ++st) {
+    for (int st = 0; st < kBatchStages; ++st) {
         grid[st] = batched_grid(p, st, &e);
         if (e != cudaSuccess) return cuda_fail(e);
     }
     if (!p->opt_graph) {
-        for (int st = 0; st < 3; ++st) {
-            const int stage = st == 0 ? GBFFT_STAGE_ROWS_FWD : st == 1 ? GBFFT_STAGE_COLS : GBFFT_STAGE_ROWS_INV;
+        for (int st : kBatchOrder) {
+            const int stage = st == 0   ? GBFFT_STAGE_ROWS_FWD
+                              : st == 1 ? GBFFT_STAGE_COLS
+                              : st == 2 ? GBFFT_STAGE_ROWS_INV
+                                        : GBFFT_STAGE_FILTER_PREP;
             rc = launch(p, stage, s, [&] {
                 return launch_batched_stage(st, grid[st], p->bsmem[st],
                                             reinterpret_cast<const BatchImage *>(p->ws + p->off_bimgs),
@@ -777,8 +770,9 @@ int fft2_filter_ifft2_batched(gbfft_plan_t p, const gbfft_image_ptrs *images, gb
         }
         return GBFFT_OK;
     }
-    if (!p->graph_exec || p->graph_ptrs != images || p->graph_grid[0] != grid[0] || p->graph_grid[1] != grid[1] ||
-        p->graph_grid[2] != grid[2]) {
+    bool same_grid = true;
+    for (int st = 0; st < kBatchStages; ++st) same_grid = same_grid && p->graph_grid[st] == grid[st];
+    if (!p->graph_exec || p->graph_ptrs != images || !same_grid) {
         drop_graph(p);
         if (!p->cap_stream && (e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking)) != cudaSuccess)
             return cuda_fail(e);
@@ -798,7 +792,7 @@ int fft2_filter_ifft2_batched(gbfft_plan_t p, const gbfft_image_ptrs *images, gb
             return cuda_fail(e);
         }
         p->graph_ptrs = images;
-        for (int st = 0; st < 3; ++st) p->graph_grid[st] = grid[st];
+        for (int st = 0; st < kBatchStages; ++st) p->graph_grid[st] = grid[st];
     }
     return launch(p, GBFFT_STAGE_GRAPH, s, [&] { return cudaGraphLaunch(p->graph_exec, s); });
 }
@@ -816,23 +810,24 @@ int fft_plan_autotune(gbfft_plan_t p, const void *args, gbfft_stream_t stream) {
     if (e == cudaSuccess) e = cudaEventCreate(&b);
     if (e != cudaSuccess) return cuda_fail(e);
     const int nsm = sm_count();
-    int grid[3], fits[3] = {1, 1, 1};
+    int grid[kBatchStages], fits[kBatchStages] = {1, 1, 1, 1};
     // occupancy of every stage first: this also sets each kernel's shared
     // memory attributes, which every launch below needs
-    for (int st = 0; st < 3 && e == cudaSuccess; ++st) {
+    for (int st = 0; st < kBatchStages && e == cudaSuccess; ++st) {
         e = batch_max_blocks_per_sm(st, p->bsmem[st], &fits[st]);
         if (fits[st] < 1) fits[st] = 1;
     }
-    for (int st = 0; st < 3 && e == cudaSuccess; ++st) {
+    for (int st = 0; st < kBatchStages && e == cudaSuccess; ++st) {
         const int fit = fits[st];
-        for (int q = 0; q < 3; ++q) grid[q] = (p->opt_bps[q] > 0 ? (int)p->opt_bps[q] : fits[q]) * nsm;
+        for (int q = 0; q < kBatchStages; ++q) grid[q] = (p->opt_bps[q] > 0 ? (int)p->opt_bps[q] : fits[q]) * nsm;
         float best = 1e30f;
         int best_bps = fit;
         for (int bps = 1; bps <= fit && e == cudaSuccess; ++bps) {
             grid[st] = bps * nsm;
             float total = 0.f;
             for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
-                for (int q = 0; q < 3 && e == cudaSuccess; ++q) {
+                for (int q : kBatchOrder) {
+                    if (e != cudaSuccess) break;
                     if (q == st) e = cudaEventRecord(a, s);
                     if (e == cudaSuccess)
                         e = launch_batched_stage(q, grid[q], p->bsmem[q],
@@ -870,7 +865,7 @@ int fft_plan_get_option(gbfft_plan_t p, int key, int64_t *value) {
         case GBFFT_OPT_ENABLE_BACKWARD: *value = p->opt_backward; return GBFFT_OK;
         case GBFFT_OPT_BLOCKS_PER_SM:
             // three stages packed 8 bits each: forward rows | columns << 8 | inverse rows << 16
-            *value = p->opt_bps[0] | (p->opt_bps[1] << 8) | (p->opt_bps[2] << 16);
+            *value = p->opt_bps[0] | (p->opt_bps[1] << 8) | (p->opt_bps[2] << 16) | (p->opt_bps[3] << 24);
             return GBFFT_OK;
         case GBFFT_OPT_USE_GRAPH: *value = p->opt_graph; return GBFFT_OK;
         case GBFFT_OPT_ONCHIP: *value = p->opt_onchip; return GBFFT_OK;

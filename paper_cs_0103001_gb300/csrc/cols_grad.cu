@@ -68,7 +68,7 @@ __global__ void __launch_bounds__(GradCfg<N>::THREADS)
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         sl[e] = grad_slot<N, E, T>(t, e, log2g);
-        h[e] = hs[(size_t)k * N + sl[e]];
+        h[e] = hs[(size_t)k * N + t + T * e];  // the prepared filter is in row order
         acc[e] = 0.f;
         acc2[e] = 0.f;
     }
@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(GradCfg<N>::THREADS)
                 const float2 rg = make_float2(0.5f * (vg[e].y + qg.y), 0.5f * (qg.x - vg[e].x));
                 acc[e] += pg.x * px.x + pg.y * px.y;
                 acc2[e] += rg.x * rx.x + rg.y * rx.y;
-                const float bt = beta[sl[e]];
+                const float bt = beta[t + T * e];
                 vg[e] = make_float2(h[e] * vg[e].x + bt * qg.x, h[e] * vg[e].y - bt * qg.y);
             }
         }

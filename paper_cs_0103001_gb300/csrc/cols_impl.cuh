@@ -1,7 +1,8 @@
 // cols_impl.cuh — the fused column pass of the Sec. 5 pipeline.
 //
 // The row pass leaves, per image, the row half spectra column-major in slot
-// order (layout.cuh) and the prepared filter s * Hs[u][k] in the same order.
+// order (layout.cuh); the prepared filter s * Hs[u][k] is column-major in
+// row order (column k: u = 0 .. N-1), so every warp reads it contiguously.
 // One group of T threads owns one half-spectrum column k and runs, without
 // leaving the chip:
 //   column FFT (length N = rows, Eq. E2 direction, unscaled)
@@ -80,7 +81,7 @@ __device__ __forceinline__ void cols_body(float2 *spec, const float *__restrict_
     // the filter is read after the forward transform so it holds no registers during it
     float h[E];
 #pragma unroll
-    for (int e = 0; e < E; ++e) h[e] = hcol[slot_e<N, E, T>(t, e, log2g)];
+    for (int e = 0; e < E; ++e) h[e] = hcol[t + T * e];  // the prepared filter is in row order
 
     if (bx == 0) {  // the group of column 0 needs Q[-u] (uniform per block)
         __syncthreads();
@@ -97,7 +98,7 @@ __device__ __forceinline__ void cols_body(float2 *spec, const float *__restrict_
         for (int e = 0; e < E; ++e) {
             const int u = t + T * e;
             const float2 qm = ex[pad16((N - u) & (N - 1))];
-            const float bt = bcol[slot_e<N, E, T>(t, e, log2g)];
+            const float bt = bcol[u];
             v[e] = make_float2(h[e] * v[e].x + bt * qm.x, h[e] * v[e].y - bt * qm.y);
         }
     }

@@ -53,18 +53,6 @@ cudaError_t launch_fourstep_b(const void *tmp, void *out, int log2n, long long b
 // [cols/2][rows] complex64, column-major in slot order (layout.cuh; column 0
 // packs (DC, Nyquist) of each real row); prepared filter s * Hs [cols/2][rows]
 // float32 in the same order (column 0: alpha) and beta [rows].
-struct RowsFwdArgs {
-    const float *img;   // [nimg][rows][cols]
-    void *spec;         // [nimg][cols/2][rows] complex64
-    int rows, cols, nimg;
-    const float *H;     // filter of image 0 of this launch (row-major [rows][cols])
-    float *hs;          // prepared filter (one, or one per image when filter_mode == 2)
-    float *beta;
-    long long h_stride; // elements between consecutive images' filters (filter_mode 2)
-    int filter_mode;    // 0: none, 1: one shared filter (prepared by image 0), 2: per image
-    float scale;        // s = 1/(rows * cols)
-    const void *tw;     // twiddles of length cols
-};
 int rows_pairs_per_block(int cols);
 // Row passes of zero-padded images: fwd reads nimg in_rows x in_cols images
 // (contiguous, pitch in_cols) as the top-left corner of rows x cols grids into
@@ -76,9 +64,12 @@ cudaError_t launch_rows_pad(bool fwd, const void *src, void *dst, int rows, int 
 // the Nyquist column into nyq [rows], both in slot order.
 cudaError_t launch_cols_spectrum(const void *spec, float *mag_T, float *nyq, float scale, int rows, int cols,
                                  const void *tw_rows, cudaStream_t s);
-cudaError_t launch_rows_fwd(const RowsFwdArgs &a, cudaStream_t s);
-// Prepared filter alone (same values as RowsFwdArgs filter_mode 1/2) for nimg
-// filters H + i * h_stride into hs + i * hs_img, beta + i * beta_img.
+// Forward row pass: nimg real images [rows][cols] -> half spectra
+// [nimg][cols/2][rows] complex64, slot order (layout.cuh).
+cudaError_t launch_rows_fwd(const float *img, void *spec, int rows, int cols, int nimg, const void *tw_cols,
+                            cudaStream_t s);
+// Prepared filter (rows_impl.cuh) for nimg filters H + i * h_stride into
+// hs + i * hs_img, beta + i * beta_img.
 cudaError_t launch_filter_prep(const float *H, float *hs, float *beta, int rows, int cols, int nimg, float scale,
                                long long h_stride, long long hs_img, long long beta_img, cudaStream_t s);
 // hs_img / beta_img: elements between images' prepared filters (0 = shared)

@@ -95,20 +95,10 @@ extern "C" int fft2_filter_ifft2_noalloc(int64_t rows, int64_t cols, int64_t bat
     }
     const long long np = rows * cols;
     for (long long b = 0; b < batch; ++b) {
-        RowsFwdArgs a;
-        a.img = img + b * np;
-        a.spec = spec;
-        a.rows = (int)rows;
-        a.cols = (int)cols;
-        a.nimg = 1;
-        a.H = H + b * h_batch_stride;
-        a.hs = hs;
-        a.beta = beta;
-        a.h_stride = 0;
-        a.filter_mode = (b == 0 || h_batch_stride != 0) ? 1 : 0;  // prepare each filter once
-        a.scale = (float)(1.0 / (double)np);
-        a.tw = tw_c;
-        e = launch_rows_fwd(a, s);
+        if (b == 0 || h_batch_stride != 0)  // prepare each filter once
+            e = launch_filter_prep(H + b * h_batch_stride, hs, beta, (int)rows, (int)cols, 1,
+                                   (float)(1.0 / (double)np), 0, 0, 0, s);
+        if (e == cudaSuccess) e = launch_rows_fwd(img + b * np, spec, (int)rows, (int)cols, 1, tw_c, s);
         if (e == cudaSuccess) e = launch_cols_filter(spec, hs, beta, 0, 0, (int)rows, (int)cols, 1, tw_r, s);
         if (e == cudaSuccess) e = launch_rows_inv(spec, out + b * np, (int)rows, (int)cols, 1, tw_c, s);
         if (e != cudaSuccess) return GBFFT_ERR_CUDA;

@@ -10,12 +10,6 @@
 // each block stages its rows' values in shared memory and writes 2G
 // consecutive slots of every column.
 //
-// The forward pass also prepares the filter for the column pass: for its
-// pair of mirror rows u = a, b it reads filter rows u and -u once and writes
-// s * Hs[u][k] (s = 1/(N M), Hs the even part of H) for k = 1..M/2-1 and, for
-// the packed column 0, alpha = s (h0 + h1) / 2 and beta = s (h0 - h1) / 2 with
-// h0 = Hs[u][0], h1 = Hs[u][M/2].
-//
 // The inverse pass reads its rows' slots back, rebuilds Z[k] = A[k] + i B[k]
 // for all k (A[M-k] = conj A[k]), runs one unscaled inverse FFT (Eq. E3) and
 // writes Re z to row a and Im z to row b.
@@ -49,18 +43,15 @@ template <int M> struct RowCfg {
 
 // One block's share of the forward row pass: row pairs bx*G .. bx*G + G - 1 of
 // one image.  img: the image [N][M]; spec: its half spectra [M/2][N] (slot
-// order); with `prep`, also the prepared filter of frequency rows of those
-// pairs from H (row-major [N][M]) into hs [M/2][N] and beta [N].  Every thread
-// of the block must call it; it ends after a block-wide barrier-free epilogue,
-// so a caller that reuses shared memory must synchronise first.
+// order).  Every thread of the block must call it; it ends after a
+// block-wide barrier-free epilogue, so a caller that reuses shared memory
+// must synchronise first.
 // With PAD, img is the crop.rows x crop.cols sub-image (pitch crop.cols) and
 // the rest of the grid reads as zero.
 template <int M, typename FFT = Fp32Fft, bool PAD = false>
-__device__ __forceinline__ void rows_fwd_body(const float *__restrict__ img, float2 *__restrict__ spec,
-                                              const float *__restrict__ H, float *__restrict__ hs,
-                                              float *__restrict__ beta, int N, int log2g, bool prep, float scale,
-                                              const float2 *__restrict__ tw, int bx, unsigned char *smraw,
-                                              FFT fft = FFT(), Crop crop = Crop{0, 0}) {
+__device__ __forceinline__ void rows_fwd_body(const float *__restrict__ img, float2 *__restrict__ spec, int N,
+                                              int log2g, const float2 *__restrict__ tw, int bx,
+                                              unsigned char *smraw, FFT fft = FFT(), Crop crop = Crop{0, 0}) {
     typedef RowCfg<M> K;
     constexpr int E = K::E, T = K::T, SR = K::SR, H2 = M / 2;
     float2 *sm = reinterpret_cast<float2 *>(smraw);
@@ -133,41 +124,6 @@ __device__ __forceinline__ void rows_fwd_body(const float *__restrict__ img, flo
             const float2 x0 = stg[k * SR + s], x1 = stg[k * SR + s + 1];
             *reinterpret_cast<float4 *>(sb + (size_t)k * N + s) = make_float4(x0.x, x0.y, x1.x, x1.y);
         }
-    }
-    if (!prep) return;  // uniform per block
-
-    // ---- filter preparation for frequency rows a and b
-    const float *hb = H;
-    float *stf = reinterpret_cast<float *>(smraw);
-    __syncthreads();  // staging reads done
-    if (active) {
-        const int ma = (N - a) & (N - 1), mb = (N - b) & (N - 1);
-        const float *Ha = hb + (size_t)a * M, *Hma = hb + (size_t)ma * M;
-        const float *Hb = hb + (size_t)b * M, *Hmb = hb + (size_t)mb * M;
-#pragma unroll
-        for (int e = 0; e < E / 2; ++e) {
-            const int k = t + T * e;
-            if (e == 0 && t == 0) {
-                const float h0a = 0.5f * (Ha[0] + Hma[0]), h1a = 0.5f * (Ha[H2] + Hma[H2]);
-                const float h0b = 0.5f * (Hb[0] + Hmb[0]), h1b = 0.5f * (Hb[H2] + Hmb[H2]);
-                stf[g] = 0.5f * scale * (h0a + h1a);
-                stf[G + g] = 0.5f * scale * (h0b + h1b);
-                float *bb = beta + (size_t)bx * 2 * G;
-                bb[g] = 0.5f * scale * (h0a - h1a);
-                bb[G + g] = 0.5f * scale * (h0b - h1b);
-            } else {
-                const int km = M - k;
-                stf[k * SR + g] = 0.5f * scale * (Ha[k] + Hma[km]);
-                stf[k * SR + G + g] = 0.5f * scale * (Hb[k] + Hmb[km]);
-            }
-        }
-    }
-    __syncthreads();
-    float *hsb = hs + (size_t)bx * 2 * G;
-    const int n = H2 << (log2g + 1);
-    for (int idx = threadIdx.x; idx < n; idx += K::THREADS) {
-        const int k = idx >> (log2g + 1), s = idx & (2 * G - 1);
-        hsb[(size_t)k * N + s] = stf[k * SR + s];
     }
 }
 
@@ -253,5 +209,90 @@ __device__ __forceinline__ void rows_inv_body(const float2 *__restrict__ spec, f
         }
     }
 }
+
+// ---- filter preparation ------------------------------------------------
+// The column pass multiplies half-spectrum column k by s * Hs[u][k] (s =
+// 1/(N M), Hs[u][k] = (H[u][k] + H[-u][-k]) / 2, the even part of the filter:
+// the real part of the pipeline's output only sees it) and, in the packed
+// column 0, uses alpha = s (h0 + h1) / 2 and beta = s (h0 - h1) / 2 with
+// h0 = Hs[u][0], h1 = Hs[u][M/2].  They are prepared column-major in row
+// order: hs[k][u] (alpha in k = 0), beta[u].
+constexpr int kPrepRows = 32, kPrepCols = 64;  // tile of the preparation
+
+// One tile of the filter preparation (block-wide; blockDim.x threads): rows
+// u0 .. u0 + R - 1, half-spectrum columns k0 .. k0 + K - 1 (K = 2^log2k) of
+// one filter H into hs (row order) and beta; `tile` is K (R + 1) floats of
+// shared memory.  Ends with the tile's global writes (no trailing barrier).
+template <int R, bool QUADS>
+__device__ __forceinline__ void filter_prep_tile(const float *__restrict__ hb, float *__restrict__ hsz,
+                                                 float *__restrict__ betaz, int N, int M, int log2k, float scale,
+                                                 int u0, int k0, float *tile) {
+    constexpr int SR = R + 1;  // tile row stride (odd: conflict-free column writes)
+    const int K = 1 << log2k, H2 = M >> 1;
+    const float hsc = 0.5f * scale;
+
+    if (QUADS) {
+        // unit = (row r, four consecutive columns); the mirror run [M-k-3, M-k]
+        // comes from two aligned quads (for k = 0 the element M - k is column 0)
+        const int nq = K >> 2, units = R << (log2k - 2);
+#pragma unroll 2
+        for (int q = threadIdx.x; q < units; q += blockDim.x) {
+            const int r = q >> (log2k - 2), kq = (q & (nq - 1)) << 2;
+            const int u = u0 + r, mu = (N - u) & (N - 1);
+            const int k = k0 + kq;
+            const float *Hu = hb + (size_t)u * M, *Hm = hb + (size_t)mu * M;
+            const float4 f = __ldcs(reinterpret_cast<const float4 *>(Hu + k));
+            const float4 m1 = __ldcs(reinterpret_cast<const float4 *>(Hm + (M - k - 4)));
+            const float m0 = k == 0 ? Hm[0] : __ldcs(Hm + (M - k));
+            float v0;
+            if (k == 0) {
+                const float h0 = 0.5f * (f.x + m0), h1 = 0.5f * (Hu[H2] + Hm[H2]);
+                v0 = hsc * (h0 + h1);
+                betaz[u] = hsc * (h0 - h1);
+            } else {
+                v0 = hsc * (f.x + m0);
+            }
+            float *tc = tile + kq * SR + r;
+            tc[0] = v0;
+            tc[SR] = hsc * (f.y + m1.w);
+            tc[2 * SR] = hsc * (f.z + m1.z);
+            tc[3 * SR] = hsc * (f.w + m1.y);
+        }
+    } else {
+        const int n = R << log2k;
+        for (int idx = threadIdx.x; idx < n; idx += blockDim.x) {
+            const int r = idx >> log2k, i = idx & (K - 1);
+            const int u = u0 + r, mu = (N - u) & (N - 1);
+            const int k = k0 + i;
+            const float *Hu = hb + (size_t)u * M, *Hm = hb + (size_t)mu * M;
+            float v;
+            if (k == 0) {
+                const float h0 = 0.5f * (Hu[0] + Hm[0]), h1 = 0.5f * (Hu[H2] + Hm[H2]);
+                v = hsc * (h0 + h1);
+                betaz[u] = hsc * (h0 - h1);
+            } else {
+                v = hsc * (__ldcs(Hu + k) + __ldcs(Hm + (M - k)));
+            }
+            tile[i * SR + r] = v;
+        }
+    }
+    __syncthreads();
+    float *hsb = hsz + u0;
+    if (QUADS) {  // four rows per store: R >= 4 and u0 a multiple of R
+        const int m = K * (R / 4);
+        for (int idx = threadIdx.x; idx < m; idx += blockDim.x) {
+            const int i = idx / (R / 4), r = (idx % (R / 4)) * 4;
+            const float *tr = tile + i * SR + r;
+            *reinterpret_cast<float4 *>(hsb + (size_t)(k0 + i) * N + r) = make_float4(tr[0], tr[1], tr[2], tr[3]);
+        }
+    } else {
+        const int m = K * R;
+        for (int idx = threadIdx.x; idx < m; idx += blockDim.x) {
+            const int i = idx / R, r = idx % R;
+            hsb[(size_t)(k0 + i) * N + r] = tile[i * SR + r];
+        }
+    }
+}
+
 
 }  // namespace gbfft

@@ -33,8 +33,7 @@ __global__ void __launch_bounds__(RowCfg<M>::THREADS, 1)
     extern __shared__ __align__(16) unsigned char smraw[];
     const size_t y = blockIdx.y;
     TcFft<TERMS> f = make_tc<RowCfg<M>::THREADS, TERMS>(smraw, RowCfg<M>::SMEM);
-    rows_fwd_body<M, TcFft<TERMS>>(img + y * N * M, spec + y * (M / 2) * N, nullptr, nullptr, nullptr, N, log2g,
-                                   false, 0.f, tw, blockIdx.x, smraw, f);
+    rows_fwd_body<M, TcFft<TERMS>>(img + y * N * M, spec + y * (M / 2) * N, N, log2g, tw, blockIdx.x, smraw, f);
 }
 
 template <int M, int TERMS>
