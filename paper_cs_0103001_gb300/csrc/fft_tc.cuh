@@ -12,11 +12,11 @@
 // In real arithmetic Yr = Fr Xr - Fi Xi and Yi = Fi Xr + Fr Xi.
 //
 // Data path of a pass, per warp (32 butterflies, one per thread): twiddle in
-// FP32 as in fft_core.cuh; then four rounds of 8 butterflies: the 8 owning
-// threads write their split inputs to a small warp-private staging area, the
-// warp runs the MMAs, and the accumulators (output k = g, g + 8 of butterflies
-// 2 tq, 2 tq + 1, with g = lane / 4, tq = lane mod 4) go straight to their
-// Stockham destinations in the exchange buffer.
+// FP32 as in fft_core.cuh; every thread splits its butterfly's inputs and
+// writes them to the warp-private staging area (four groups of 8 butterflies);
+// then, for each group, the warp runs the MMAs and the accumulators (output
+// k = g, g + 8 of butterflies 2 tq, 2 tq + 1, with g = lane / 4, tq = lane mod
+// 4) go straight to their Stockham destinations in the exchange buffer.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -67,11 +67,14 @@ __device__ __forceinline__ void mma_bf16_16816(float (&d)[4], const uint32_t (&a
 
 // Per-thread operand state: A fragments of Fr = cos and Fs = sin (each split
 // term; the pass applies the sign of its direction) and the warp's staging
-// area (TERMS x {re, im} planes of 8 rows x 12 words).
+// area: for each of the 4 groups of 8 butterflies, TERMS x {re, im} planes of
+// 8 rows x 12 words.
 template <int TERMS> struct TcState {
     uint32_t fr[TERMS][4], fi[TERMS][4];
     uint32_t *stg;
-    static constexpr int WORDS_PER_WARP = 2 * TERMS * 8 * 12;
+    static constexpr int PLANE = 8 * 12;                 // words per plane
+    static constexpr int GROUP = 2 * TERMS * PLANE;      // words per group of 8 butterflies
+    static constexpr int WORDS_PER_WARP = 4 * GROUP;
 };
 
 // A[k][n] = F[k][n] for the thread's fragment slots: reg0 (g, 2tq..2tq+1),
@@ -117,41 +120,44 @@ __device__ __forceinline__ void tc_pass16(float2 (&v)[16], float2 *sm, const flo
     }
     const int lane = t & 31, g = lane >> 2, tq = lane & 3;
     const int warp_base = t - lane;
+    constexpr int PLANE = TcState<TERMS>::PLANE, GROUP = TcState<TERMS>::GROUP;
+    // every lane splits its own butterfly's 16 inputs and stages them as row
+    // (lane mod 8) of group (lane / 8): plane 2i = re part i, 2i+1 = im part i
+    {
+        uint32_t *row = st.stg + (lane >> 3) * GROUP + (lane & 7) * 12;
+#pragma unroll
+        for (int i = 0; i < TERMS; ++i) {
+            uint32_t wr[8], wi[8];
+#pragma unroll
+            for (int w = 0; w < 8; ++w) {
+                __nv_bfloat16 a[TERMS], b[TERMS], c[TERMS], d[TERMS];
+                bf16_split<TERMS>(v[2 * w].x, a);
+                bf16_split<TERMS>(v[2 * w + 1].x, b);
+                bf16_split<TERMS>(v[2 * w].y, c);
+                bf16_split<TERMS>(v[2 * w + 1].y, d);
+                wr[w] = pack_bf16(a[i], b[i]);
+                wi[w] = pack_bf16(c[i], d[i]);
+            }
+            uint4 *pr = reinterpret_cast<uint4 *>(row + (2 * i) * PLANE);
+            uint4 *pi = reinterpret_cast<uint4 *>(row + (2 * i + 1) * PLANE);
+            pr[0] = make_uint4(wr[0], wr[1], wr[2], wr[3]);
+            pr[1] = make_uint4(wr[4], wr[5], wr[6], wr[7]);
+            pi[0] = make_uint4(wi[0], wi[1], wi[2], wi[3]);
+            pi[1] = make_uint4(wi[4], wi[5], wi[6], wi[7]);
+        }
+    }
+    __syncwarp();
     __syncthreads();  // the previous exchange's reads are complete
-    constexpr int PLANE = 8 * 12;  // words per plane
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        if ((lane >> 3) == q) {  // the 8 owners stage their rows: plane 2i = re part i, 2i+1 = im part i
-            const int row = lane & 7;
-#pragma unroll
-            for (int i = 0; i < TERMS; ++i) {
-                uint32_t wr[8], wi[8];
-#pragma unroll
-                for (int w = 0; w < 8; ++w) {
-                    __nv_bfloat16 a[TERMS], b[TERMS], c[TERMS], d[TERMS];
-                    bf16_split<TERMS>(v[2 * w].x, a);
-                    bf16_split<TERMS>(v[2 * w + 1].x, b);
-                    bf16_split<TERMS>(v[2 * w].y, c);
-                    bf16_split<TERMS>(v[2 * w + 1].y, d);
-                    wr[w] = pack_bf16(a[i], b[i]);
-                    wi[w] = pack_bf16(c[i], d[i]);
-                }
-                uint4 *pr = reinterpret_cast<uint4 *>(st.stg + (2 * i) * PLANE + row * 12);
-                uint4 *pi = reinterpret_cast<uint4 *>(st.stg + (2 * i + 1) * PLANE + row * 12);
-                pr[0] = make_uint4(wr[0], wr[1], wr[2], wr[3]);
-                pr[1] = make_uint4(wr[4], wr[5], wr[6], wr[7]);
-                pi[0] = make_uint4(wi[0], wi[1], wi[2], wi[3]);
-                pi[1] = make_uint4(wi[4], wi[5], wi[6], wi[7]);
-            }
-        }
-        __syncwarp();
+        const uint32_t *gs = st.stg + q * GROUP;
         uint32_t xr[TERMS][2], xi[TERMS][2];
 #pragma unroll
         for (int i = 0; i < TERMS; ++i) {
-            xr[i][0] = st.stg[(2 * i) * PLANE + g * 12 + tq];
-            xr[i][1] = st.stg[(2 * i) * PLANE + g * 12 + tq + 4];
-            xi[i][0] = st.stg[(2 * i + 1) * PLANE + g * 12 + tq];
-            xi[i][1] = st.stg[(2 * i + 1) * PLANE + g * 12 + tq + 4];
+            xr[i][0] = gs[(2 * i) * PLANE + g * 12 + tq];
+            xr[i][1] = gs[(2 * i) * PLANE + g * 12 + tq + 4];
+            xi[i][0] = gs[(2 * i + 1) * PLANE + g * 12 + tq];
+            xi[i][1] = gs[(2 * i + 1) * PLANE + g * 12 + tq + 4];
         }
         // F = cos + DIR i sin:  Yr = cos Xr - DIR sin Xi,  Yi = DIR sin Xr + cos Xi
         float yr[4] = {0.f, 0.f, 0.f, 0.f}, yi[4] = {0.f, 0.f, 0.f, 0.f};
@@ -175,8 +181,8 @@ __device__ __forceinline__ void tc_pass16(float2 (&v)[16], float2 *sm, const flo
             sm[pad16(base + g * NS) * S] = make_float2(yr[c], yi[c]);
             sm[pad16(base + (g + 8) * NS) * S] = make_float2(yr[2 + c], yi[2 + c]);
         }
-        __syncwarp();  // staging is rewritten by the next round
     }
+    __syncwarp();  // the staging area is rewritten by the next pass
     __syncthreads();
 #pragma unroll
     for (int e = 0; e < 16; ++e) v[e] = sm[pad16(t + T * e) * S];

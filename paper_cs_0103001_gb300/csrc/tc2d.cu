@@ -47,7 +47,7 @@ __global__ void __launch_bounds__(RowCfg<M>::THREADS, 1)
 }
 
 template <int N, int TERMS>
-__global__ void __launch_bounds__(ColCfg<N>::THREADS, 1)
+__global__ void __launch_bounds__(ColCfg<N>::THREADS, 2)
     k_cols_tc(float2 *spec, const float *__restrict__ hs, const float *__restrict__ beta, long long hs_img,
               long long beta_img, int M, int log2g, const float2 *__restrict__ tw) {
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -91,7 +91,7 @@ static cudaError_t cols_tc(void *spec, const float *hs, const float *beta, long 
                            int cols, int nimg, const void *tw, cudaStream_t s) {
     typedef ColCfg<N> K;
     const size_t smem = K::SMEM + tc_stage_bytes<K::THREADS, TERMS>();
-    cudaError_t e = set_smem_attrs((const void *)k_cols_tc<N, TERMS>, smem, 1);
+    cudaError_t e = set_smem_attrs((const void *)k_cols_tc<N, TERMS>, smem, 2);
     if (e != cudaSuccess) return e;
     int g = rows_pairs_per_block(cols);
     if (g > N / 2) g = N / 2;
