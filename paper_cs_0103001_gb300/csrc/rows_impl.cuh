@@ -7,8 +7,8 @@
 // A real row has a Hermitian spectrum, so only bins 0..M/2 are kept; A[0] and
 // A[M/2] are real and share one complex slot (re = DC, im = Nyquist).  The
 // half spectra go to the workspace column-major in slot order (layout.cuh):
-// each block stages its rows' values in shared memory and writes 2G
-// consecutive slots of every column.
+// each block keeps its rows' transforms in shared memory and writes 2G
+// consecutive slots of every column, separating the spectra as it stores.
 //
 // The inverse pass reads its rows' slots back, rebuilds Z[k] = A[k] + i B[k]
 // for all k (A[M-k] = conj A[k]), runs one unscaled inverse FFT (Eq. E3) and
@@ -40,6 +40,22 @@ template <int M> struct RowCfg {
     static constexpr int STAGE = (M / 2) * SR;
     static constexpr size_t SMEM = (size_t)(EXCH > STAGE ? EXCH : STAGE) * sizeof(float2);
 };
+
+// A[k] (side false) or B[k] (side true) of a row pair from its transform Z
+// in exchange buffer exg (element x at exg[pad16(x)]):
+//   A = (Z[k] + conj Z[M-k]) / 2,  B = (Z[k] - conj Z[M-k]) / (2i);
+// k = 0 packs the real DC and Nyquist bins as (re, im).
+template <int M>
+__device__ __forceinline__ float2 split_ab(const float2 *exg, int k, bool side) {
+    const float2 zk = exg[pad16(k)];
+    if (k == 0) {
+        const float2 zn = exg[pad16(M / 2)];
+        return side ? make_float2(zk.y, zn.y) : make_float2(zk.x, zn.x);
+    }
+    const float2 zm = exg[pad16(M - k)];
+    return side ? make_float2(0.5f * (zk.y + zm.y), 0.5f * (zm.x - zk.x))
+                : make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+}
 
 // One block's share of the forward row pass: row pairs bx*G .. bx*G + G - 1 of
 // one image.  img: the image [N][M]; spec: its half spectra [M/2][N] (slot
@@ -88,41 +104,24 @@ __device__ __forceinline__ void rows_fwd_body(const float *__restrict__ img, flo
 #pragma unroll
     for (int e = 0; e < E; ++e) ex[pad16(t + T * e)] = v[e];
     __syncthreads();
-    // split the two rows' spectra: ab[e] = A[k], ab[E/2 + e] = B[k], k = t + T e
-    float2 ab[E];
-#pragma unroll
-    for (int e = 0; e < E / 2; ++e) {
-        const int k = t + T * e;
-        const float2 zk = v[e];
-        if (e == 0 && t == 0) {
-            const float2 zn = v[E / 2];  // Z[M/2]
-            ab[e] = make_float2(zk.x, zn.x);
-            ab[E / 2 + e] = make_float2(zk.y, zn.y);
-        } else {
-            const float2 zm = ex[pad16(M - k)];
-            ab[e] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
-            ab[E / 2 + e] = make_float2(0.5f * (zk.y + zm.y), 0.5f * (zm.x - zk.x));
-        }
-    }
-    __syncthreads();  // exchange buffers are reused as the staging area
-    float2 *stg = sm;
-    if (active) {
-#pragma unroll
-        for (int e = 0; e < E / 2; ++e) {
-            const int k = t + T * e;
-            stg[k * SR + g] = ab[e];
-            stg[k * SR + G + g] = ab[E / 2 + e];
-        }
-    }
-    __syncthreads();
-    {
-        // two slots (16 bytes) per thread; 2G >= 2 and every run starts 16-byte aligned
-        float2 *sb = spec + (size_t)bx * 2 * G;
+    // split the two rows' spectra while storing: a unit is column k and two
+    // consecutive slots s, s + 1 of the block's run of 2G (s < G: A of pairs
+    // s, s + 1; s >= G: B of pairs s - G, s - G + 1), 16 bytes per store
+    float2 *sb = spec + (size_t)bx * 2 * G;
+    if (G >= 2) {
         const int n = H2 << log2g;
         for (int idx = threadIdx.x; idx < n; idx += K::THREADS) {
             const int k = idx >> log2g, s = (idx & (G - 1)) * 2;
-            const float2 x0 = stg[k * SR + s], x1 = stg[k * SR + s + 1];
+            const bool side = s >= G;
+            const int g0 = side ? s - G : s;
+            const float2 x0 = split_ab<M>(sm + g0 * padded_len(M), k, side);
+            const float2 x1 = split_ab<M>(sm + (g0 + 1) * padded_len(M), k, side);
             *reinterpret_cast<float4 *>(sb + (size_t)k * N + s) = make_float4(x0.x, x0.y, x1.x, x1.y);
+        }
+    } else {  // one pair per block (N = 2): its A and B side by side
+        for (int k = threadIdx.x; k < H2; k += K::THREADS) {
+            const float2 a = split_ab<M>(sm, k, false), b = split_ab<M>(sm, k, true);
+            *reinterpret_cast<float4 *>(sb + (size_t)k * N) = make_float4(a.x, a.y, b.x, b.y);
         }
     }
 }
