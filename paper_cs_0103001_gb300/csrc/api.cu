@@ -725,11 +725,11 @@ int fft2_batched_plan_create(int count, const int64_t *rows, const int64_t *cols
         const int nprep = batch_prep_tiles(im.rows, im.cols);
         const double cprep = (double)im.rows * im.cols / 2 / nprep;
         for (int bx = 0; bx < nprep; ++bx) work[3].push_back({cprep, {i, bx}});
-        p->bsmem[0] = std::max(p->bsmem[0], batch_row_smem(im.cols));
+        p->bsmem[0] = std::max(p->bsmem[0], batch_row_smem(im.cols, true));
+        p->bsmem[2] = std::max(p->bsmem[2], batch_row_smem(im.cols, false));
         p->bsmem[1] = std::max(p->bsmem[1], batch_col_smem(im.rows));
         p->bsmem[3] = std::max(p->bsmem[3], batch_prep_smem(im.rows, im.cols));
     }
-    p->bsmem[2] = p->bsmem[0];
     for (int st = 0; st < kBatchStages; ++st) {
         // largest first; equal costs keep image order
         std::stable_sort(work[st].begin(), work[st].end(),

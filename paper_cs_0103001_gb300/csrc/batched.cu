@@ -135,10 +135,10 @@ int batch_row_pairs(int cols) {
     }
 }
 
-size_t batch_row_smem(int cols) {
+size_t batch_row_smem(int cols, bool fwd) {
     switch (ilog2(cols)) {
 #define GBFFT_C(L) \
-    case L: return RowCfg<(1 << L)>::SMEM;
+    case L: return fwd ? RowCfg<(1 << L)>::SMEM_FWD : RowCfg<(1 << L)>::SMEM;
         GBFFT_BATCH_SIZES(GBFFT_C)
 #undef GBFFT_C
         default: return 0;

@@ -39,7 +39,7 @@ struct BatchItem {
 };
 
 int batch_row_pairs(int cols);
-size_t batch_row_smem(int cols);
+size_t batch_row_smem(int cols, bool fwd);
 int batch_col_width(int rows);
 size_t batch_col_smem(int rows);
 // filter-preparation tiles of an image: count, and shared memory of one

@@ -99,8 +99,8 @@ cudaError_t launch_filter_prep(const float *H, float *hs, float *beta, int rows,
     }
 }
 
-template <int M> static cudaError_t set_smem(const void *kern) {
-    return set_smem_attrs(kern, RowCfg<M>::SMEM, RowCfg<M>::THREADS <= 512 ? 2 : 1);
+template <int M> static cudaError_t set_smem(const void *kern, size_t smem) {
+    return set_smem_attrs(kern, smem, RowCfg<M>::THREADS <= 512 ? 2 : 1);
 }
 
 static int log2_pairs_per_block(int rows, int cols) {
@@ -112,11 +112,11 @@ static int log2_pairs_per_block(int rows, int cols) {
 template <int M>
 static cudaError_t run_rows_fwd(const float *img, void *spec, int rows, int nimg, const void *tw, cudaStream_t s) {
     typedef RowCfg<M> K;
-    cudaError_t e = set_smem<M>((const void *)k_rows_fwd<M>);
+    cudaError_t e = set_smem<M>((const void *)k_rows_fwd<M>, K::SMEM_FWD);
     if (e != cudaSuccess) return e;
     const int lg = log2_pairs_per_block(rows, M);
     dim3 grid((rows / 2) >> lg, nimg);
-    k_rows_fwd<M><<<grid, K::THREADS, K::SMEM, s>>>(img, static_cast<float2 *>(spec), rows, lg,
+    k_rows_fwd<M><<<grid, K::THREADS, K::SMEM_FWD, s>>>(img, static_cast<float2 *>(spec), rows, lg,
                                                     static_cast<const float2 *>(tw));
     return cudaGetLastError();
 }
@@ -124,7 +124,7 @@ static cudaError_t run_rows_fwd(const float *img, void *spec, int rows, int nimg
 template <int M>
 static cudaError_t run_rows_inv(const void *spec, float *out, int rows, int nimg, const void *tw, cudaStream_t s) {
     typedef RowCfg<M> K;
-    cudaError_t e = set_smem<M>((const void *)k_rows_inv<M>);
+    cudaError_t e = set_smem<M>((const void *)k_rows_inv<M>, K::SMEM);
     if (e != cudaSuccess) return e;
     const int lg = log2_pairs_per_block(rows, M);
     dim3 grid((rows / 2) >> lg, nimg);
@@ -138,17 +138,18 @@ static cudaError_t run_rows_pad(bool fwd, const void *src, void *dst, int rows, 
                                 const void *tw, cudaStream_t s) {
     typedef RowCfg<M> K;
     const void *kern = fwd ? (const void *)k_rows_fwd_pad<M> : (const void *)k_rows_inv_pad<M>;
-    cudaError_t e = set_smem<M>(kern);
+    const size_t smem = fwd ? K::SMEM_FWD : K::SMEM;
+    cudaError_t e = set_smem<M>(kern, smem);
     if (e != cudaSuccess) return e;
     const int lg = log2_pairs_per_block(rows, M);
     dim3 grid((rows / 2) >> lg, nimg);
     const Crop crop{in_rows, in_cols};
     const long long stride = (long long)in_rows * in_cols;
     if (fwd)
-        k_rows_fwd_pad<M><<<grid, K::THREADS, K::SMEM, s>>>(static_cast<const float *>(src), static_cast<float2 *>(dst),
+        k_rows_fwd_pad<M><<<grid, K::THREADS, smem, s>>>(static_cast<const float *>(src), static_cast<float2 *>(dst),
                                                              rows, lg, crop, stride, static_cast<const float2 *>(tw));
     else
-        k_rows_inv_pad<M><<<grid, K::THREADS, K::SMEM, s>>>(static_cast<const float2 *>(src), static_cast<float *>(dst),
+        k_rows_inv_pad<M><<<grid, K::THREADS, smem, s>>>(static_cast<const float2 *>(src), static_cast<float *>(dst),
                                                              rows, lg, crop, stride, static_cast<const float2 *>(tw));
     return cudaGetLastError();
 }

@@ -35,9 +35,10 @@ template <int M> struct RowCfg {
     // (32-byte runs of complex64 per column)
     static constexpr int PPC = (512 / T) > 2 ? 512 / T : 2;
     static constexpr int THREADS = PPC * T;  // 512, or 1024 for M = 8192
-    static constexpr int SR = 2 * PPC + 1;                    // staging row stride (odd: no bank conflicts)
-    static constexpr int EXCH = PPC * padded_len(M);
-    static constexpr int STAGE = (M / 2) * SR;
+    static constexpr int SR = 2 * PPC + 1;            // staging row stride (odd: no bank conflicts)
+    static constexpr int EXCH = PPC * padded_len(M);  // one exchange buffer per pair
+    static constexpr int STAGE = (M / 2) * SR;        // the inverse pass's staging of its slots
+    static constexpr size_t SMEM_FWD = (size_t)EXCH * sizeof(float2);
     static constexpr size_t SMEM = (size_t)(EXCH > STAGE ? EXCH : STAGE) * sizeof(float2);
 };
 
@@ -69,7 +70,7 @@ __device__ __forceinline__ void rows_fwd_body(const float *__restrict__ img, flo
                                               int log2g, const float2 *__restrict__ tw, int bx,
                                               unsigned char *smraw, FFT fft = FFT(), Crop crop = Crop{0, 0}) {
     typedef RowCfg<M> K;
-    constexpr int E = K::E, T = K::T, SR = K::SR, H2 = M / 2;
+    constexpr int E = K::E, T = K::T, H2 = M / 2;
     float2 *sm = reinterpret_cast<float2 *>(smraw);
     const int G = 1 << log2g;
     const int g = threadIdx.x / T;
