@@ -393,7 +393,8 @@ def run_gbfft(args):
                             "copies overlapped with compute on three streams; copies_only = the same two "
                             "copies per step with no compute (the host link's ceiling)"},
             "gpu_launches": int(round(launches_per_step * args.steps)),
-            "variants": dict(run_variants(), pipeline4096_precision=_guard(lambda: variant_precision(img, H, ref, flush)))
+            "variants": dict(run_variants(), pipeline4096_precision=_guard(lambda: variant_precision(img, H, ref, flush)),
+                             pipeline4096_analytic_filter=_guard(lambda: variant_analytic(img, flush)))
             if args.variants else None,
             "clocks": clk,
             "wall_s_timed": round(wall, 4),
@@ -520,6 +521,22 @@ def variant_pipeline256(steps: int = 200):
     res["path"] = "one cluster launch, spectra in shared memory"
     res["note"] = "us: one call from Python (host overhead included); _graph: the call replayed from a CUDA graph"
     return res
+
+
+def variant_analytic(img, flush, steps: int = 100):
+    """The headline image with the same Butterworth filter given by formula
+    (computed in the column pass: no filter read, no preparation kernel)."""
+    import torch
+
+    import paper_cs_0103001_gb300 as gb
+    from paper_cs_0103001_gb300 import _native as nat
+
+    out = torch.empty_like(img)
+    plan = gb.Plan2D(img.shape[0], img.shape[1], 1, img.device)
+    d0 = 0.1 * min(ROWS, COLS) / 2.0
+    ms = _timed(lambda: plan.filter_analytic(img, nat.FILTER_BUTTERWORTH, 4, d0, out=out), steps, 5, flush)
+    return {"us": round(ms * 1e3, 2), "gbs_44Bpx": round(METRIC_BYTES_PER_PX * ROWS * COLS / (ms * 1e-3) / 1e9, 1),
+            "filter": "butterworth order 4, D0 = 0.1 Nyquist, by formula"}
 
 
 def variant_paper_application(steps: int = 200):

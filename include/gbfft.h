@@ -198,6 +198,23 @@ int fft2_filter_ifft2(gbfft_plan_t plan, const float *img, const float *H, float
 int fft2_filter_ifft2_padded(gbfft_plan_t plan, const float *img, int64_t in_rows, int64_t in_cols, const float *H,
                              float *out, gbfft_stream_t stream);
 
+/* Analytic filters of fft2_filter_ifft2_analytic. */
+typedef enum {
+    GBFFT_FILTER_GAUSSIAN = 1,    /* exp(-|f|^2 / (2 p0^2)); p0 = sigma in bins */
+    GBFFT_FILTER_BUTTERWORTH = 2, /* 1 / (1 + (|f| / p1)^(2 p0)); p0 = order 1..16, p1 = cutoff in bins */
+    GBFFT_FILTER_DISC = 3         /* Eq. filtro: 0 where (u - rows/2)^2 + (v - cols/2)^2 <= p0^2, else 1 */
+} gbfft_filter_kind;
+
+/* fft2_filter_ifft2 with a filter given by formula instead of an array: the
+ * column pass computes H[u][v] for each bin (|f|^2 = u~^2 + v~^2 over the
+ * wrapped bins, u~ = u for u < rows/2, u - rows above), so no filter is read
+ * and none is prepared.  The three filters are even (H[-u][-v] = H[u][v]).
+ * Same layouts, batching and aliasing as fft2_filter_ifft2 (FP32 path; with
+ * GBFFT_OPT_PRECISION != 0, GBFFT_ERR_UNSUPPORTED).  GBFFT_ERR_INVALID_VALUE
+ * for an unknown kind or parameters out of range. */
+int fft2_filter_ifft2_analytic(gbfft_plan_t plan, const float *img, int kind, double p0, double p1, float *out,
+                               gbfft_stream_t stream);
+
 /* Spectrum display of Sec. 5: mag = sqrt(Re^2 + Im^2) of the 2D transform of
  * each image, zero-padded to the plan's grid as in fft2_filter_ifft2_padded
  * (in_rows = rows, in_cols = cols for no padding).  mag: batch x rows x cols

@@ -19,11 +19,13 @@ from .api import (  # noqa: F401
     clear_plan_cache,
     fft,
     fft2_filter_ifft2,
+    fft2_filter_ifft2_analytic,
     fft2_filter_ifft2_batched,
     fft2_filter_ifft2_padded,
     fft2_spectrum,
     ifft,
 )
 
-__all__ = ["fft", "ifft", "fft2_filter_ifft2", "fft2_filter_ifft2_batched", "fft2_filter_ifft2_padded",
+__all__ = ["fft", "ifft", "fft2_filter_ifft2", "fft2_filter_ifft2_analytic", "fft2_filter_ifft2_batched",
+           "fft2_filter_ifft2_padded",
            "fft2_spectrum", "Plan1D", "Plan2D", "Plan2DBatched", "clear_plan_cache"]

@@ -40,6 +40,11 @@ OPT_BLOCKS_PER_SM = 7
 OPT_USE_GRAPH = 8
 OPT_ONCHIP = 9
 
+# gbfft_filter_kind
+FILTER_GAUSSIAN = 1
+FILTER_BUTTERWORTH = 2
+FILTER_DISC = 3
+
 # gbfft_stage
 STAGES = ("fft1d", "fourstep_a", "fourstep_b", "rows_fwd", "cols_filter", "rows_inv", "cols_grad", "twiddles",
           "graph", "filter_prep", "onchip", "spectrum", "fft1d_cluster")
@@ -59,6 +64,7 @@ SIGNATURES = {
     "fft2_filter_ifft2": (_INT, [_P, _P, _P, _P, _P]),
     "fft2_filter_ifft2_padded": (_INT, [_P, _P, _I64, _I64, _P, _P, _P]),
     "fft2_spectrum": (_INT, [_P, _P, _I64, _I64, _P, _P]),
+    "fft2_filter_ifft2_analytic": (_INT, [_P, _P, _INT, ctypes.c_double, ctypes.c_double, _P, _P]),
     "fft2_filter_ifft2_backward": (_INT, [_P, _P, _P, _P, _P, _P, _P]),
     "fft_plan_destroy": (_INT, [_P]),
     "fft2_batched_plan_create": (_INT, [_INT, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_P)]),

@@ -8,6 +8,7 @@ raw device pointers.  Functions here:
   fft2_filter_ifft2(img, H) the Sec. 5 pipeline, differentiable in img and H
   fft2_filter_ifft2_padded  the same for any image size (zero padding, crop)
   fft2_spectrum(img)        the Sec. 5 spectrum display |fft2(img)|
+  fft2_filter_ifft2_analytic  the pipeline with a Gaussian, Butterworth or disc filter by formula
   Plan1D, Plan2D            explicit plans (workspace owned by a torch tensor)
 """
 
@@ -126,6 +127,18 @@ class Plan2D(_PlanBase):
         with self.lock:
             nat.call("fft2_filter_ifft2_padded", self.handle, _ptr(img), int(img.shape[-2]), int(img.shape[-1]),
                      _ptr(H), _ptr(out), _stream_handle(img.device))
+        return out
+
+    def filter_analytic(self, img: torch.Tensor, kind: int, p0: float, p1: float = 0.0,
+                        out: torch.Tensor | None = None) -> torch.Tensor:
+        """The pipeline with an analytic filter computed in the column pass
+        (nat.FILTER_GAUSSIAN: p0 = sigma; FILTER_BUTTERWORTH: p0 = order,
+        p1 = cutoff in bins; FILTER_DISC: p0 = radius of Eq. filtro)."""
+        if out is None:
+            out = torch.empty_like(img)
+        with self.lock:
+            nat.call("fft2_filter_ifft2_analytic", self.handle, _ptr(img), int(kind), float(p0), float(p1), _ptr(out),
+                     _stream_handle(img.device))
         return out
 
     def spectrum(self, img: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
@@ -323,6 +336,19 @@ def fft2_filter_ifft2_padded(img: torch.Tensor, H: torch.Tensor) -> torch.Tensor
     opts = {nat.OPT_H_BATCH_STRIDE: R * C if per_image else 0}
     plan = _cached(("2dpad", R, C, batch, per_image, img.device), lambda: Plan2D(R, C, batch, img.device, opts))
     return plan.filter_padded(img.contiguous(), H.contiguous())
+
+
+def fft2_filter_ifft2_analytic(img: torch.Tensor, kind: int, p0: float, p1: float = 0.0) -> torch.Tensor:
+    """Sec. 5 pipeline on float32 images [..., rows, cols] with a filter given
+    by formula (Gaussian, Butterworth or the disc of Eq. filtro; see
+    Plan2D.filter_analytic), computed in the column pass.  Not differentiable."""
+    _require_cuda(img, "img")
+    if img.dtype != torch.float32 or img.dim() < 2:
+        raise TypeError("img must be float32 [..., rows, cols]")
+    rows, cols = int(img.shape[-2]), int(img.shape[-1])
+    batch = img.numel() // (rows * cols)
+    plan = _cached(("2dan", rows, cols, batch, img.device), lambda: Plan2D(rows, cols, batch, img.device))
+    return plan.filter_analytic(img.contiguous(), kind, p0, p1)
 
 
 def fft2_spectrum(img: torch.Tensor, rows: int | None = None, cols: int | None = None,

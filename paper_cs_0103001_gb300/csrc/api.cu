@@ -585,6 +585,40 @@ int fft2_filter_ifft2_padded(gbfft_plan_t p, const float *img, int64_t in_rows, 
     return GBFFT_OK;
 }
 
+int fft2_filter_ifft2_analytic(gbfft_plan_t p, const float *img, int kind, double p0, double p1, float *out,
+                               gbfft_stream_t stream) {
+    int rc = check_plan_ready(p);
+    if (rc) return rc;
+    if (p->kind != KIND_2D) return GBFFT_ERR_INVALID_VALUE;
+    if (!img || !out) return GBFFT_ERR_NULL;
+    if (misaligned(img) || misaligned(out)) return GBFFT_ERR_MISALIGNED;
+    const bool ok = (kind == GBFFT_FILTER_GAUSSIAN && p0 > 0.0) ||
+                    (kind == GBFFT_FILTER_BUTTERWORTH && p0 >= 1.0 && p0 <= 16.0 && p0 == (double)(int)p0 && p1 > 0.0) ||
+                    (kind == GBFFT_FILTER_DISC && p0 >= 0.0);
+    if (!ok) return GBFFT_ERR_INVALID_VALUE;
+    if (p->opt_precision != 0) return GBFFT_ERR_UNSUPPORTED;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int rows = 1 << p->log2r, cols = 1 << p->log2c;
+    const int64_t np = (int64_t)rows * cols;
+    void *spec = p->ws + p->off_buf;
+    for (int64_t b0 = 0; b0 < p->batch; b0 += p->chunk) {
+        const int nb = (int)((p->batch - b0 < p->chunk) ? p->batch - b0 : p->chunk);
+        rc = launch(p, GBFFT_STAGE_ROWS_FWD, s, [&] {
+            return launch_rows_fwd(img + b0 * np, spec, rows, cols, nb, p->ws + p->off_tw0, s);
+        });
+        if (rc) return rc;
+        rc = launch(p, GBFFT_STAGE_COLS, s, [&] {
+            return launch_cols_analytic(spec, kind, p0, p1, rows, cols, nb, p->ws + p->off_tw1, s);
+        });
+        if (rc) return rc;
+        rc = launch(p, GBFFT_STAGE_ROWS_INV, s, [&] {
+            return launch_rows_inv(spec, out + b0 * np, rows, cols, nb, p->ws + p->off_tw0, s);
+        });
+        if (rc) return rc;
+    }
+    return GBFFT_OK;
+}
+
 int fft2_spectrum(gbfft_plan_t p, const float *img, int64_t in_rows, int64_t in_cols, float *mag,
                   gbfft_stream_t stream) {
     int rc = check_plan_ready(p);

@@ -35,9 +35,10 @@ __device__ __noinline__ void inv_case(const BatchImage &im, const gbfft_image_pt
 
 template <int L>
 __device__ __noinline__ void cols_case(const BatchImage &im, char *ws, int bx, unsigned char *sm) {
-    cols_body<(1 << L)>(reinterpret_cast<float2 *>(ws + im.spec_off), reinterpret_cast<const float *>(ws + im.hs_off),
-                        reinterpret_cast<const float *>(ws + im.beta_off), im.cols, im.log2g,
-                        reinterpret_cast<const float2 *>(ws + im.twr_off), bx, sm);
+    cols_body<(1 << L)>(reinterpret_cast<float2 *>(ws + im.spec_off),
+                        PreparedFilter{reinterpret_cast<const float *>(ws + im.hs_off),
+                                       reinterpret_cast<const float *>(ws + im.beta_off), im.rows},
+                        im.cols, im.log2g, reinterpret_cast<const float2 *>(ws + im.twr_off), bx, sm);
 }
 
 #define GBFFT_BATCH_SIZES(X) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12)

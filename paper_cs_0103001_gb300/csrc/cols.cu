@@ -1,5 +1,7 @@
 // cols.cu — launcher of the fused column pass of the Sec. 5 pipeline; the
 // kernel body and the description of the method live in cols_impl.cuh.
+#include <cmath>
+
 #include "cols_impl.cuh"
 #include "internal.h"
 
@@ -11,7 +13,17 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, 2)
                   long long beta_img, int M, int log2g, const float2 *__restrict__ tw) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const size_t y = blockIdx.y;
-    cols_body<N>(spec + y * (M / 2) * N, hs + y * hs_img, beta + y * beta_img, M, log2g, tw, blockIdx.x, smraw);
+    cols_body<N>(spec + y * (M / 2) * N, PreparedFilter{hs + y * hs_img, beta + y * beta_img, N}, M, log2g, tw,
+                 blockIdx.x, smraw);
+}
+
+// The column pass with an analytic filter (cols_impl.cuh) computed in place.
+template <int N>
+__global__ void __launch_bounds__(ColCfg<N>::THREADS, 2)
+    k_cols_analytic(float2 *spec, AnalyticFilter filt, int M, int log2g, const float2 *__restrict__ tw) {
+    extern __shared__ __align__(16) unsigned char smraw[];
+    const size_t y = blockIdx.y;
+    cols_body<N>(spec + y * (M / 2) * N, filt, M, log2g, tw, blockIdx.x, smraw);
 }
 
 // Spectrum display (Sec. 5): the column FFTs of the row half spectra, and
@@ -101,6 +113,52 @@ static cudaError_t run_cols(void *spec, const float *hs, const float *beta, long
     kern<<<grid, K::THREADS, K::SMEM, s>>>(static_cast<float2 *>(spec), hs, beta, hs_img, beta_img, cols, log2g,
                                            static_cast<const float2 *>(tw));
     return cudaGetLastError();
+}
+
+template <int N>
+static cudaError_t run_cols_analytic(void *spec, const AnalyticFilter &f, int cols, int nimg, int log2g, const void *tw,
+                                     cudaStream_t s) {
+    typedef ColCfg<N> K;
+    cudaError_t e = set_smem_attrs((const void *)k_cols_analytic<N>, K::SMEM, 2);
+    if (e != cudaSuccess) return e;
+    dim3 grid((cols / 2 + K::W - 1) / K::W, nimg);
+    k_cols_analytic<N><<<grid, K::THREADS, K::SMEM, s>>>(static_cast<float2 *>(spec), f, cols, log2g,
+                                                         static_cast<const float2 *>(tw));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_cols_analytic(void *spec, int kind, double p0, double p1, int rows, int cols, int nimg,
+                                 const void *tw_rows, cudaStream_t s) {
+    AnalyticFilter f;
+    f.kind = kind;
+    f.N = rows;
+    f.M = cols;
+    f.s = (float)(1.0 / ((double)rows * cols));
+    f.order = 0;
+    f.p = 0.f;
+    f.q = 0;
+    if (kind == 1) {
+        f.p = (float)(1.0 / (2.0 * p0 * p0));
+    } else if (kind == 2) {
+        f.order = (int)p0;
+        f.p = (float)(1.0 / (p1 * p1));
+    } else if (kind == 3) {
+        const double b2 = std::floor(p0 * p0);
+        f.q = b2 > 2147483647.0 ? 2147483647 : (int)b2;
+    } else {
+        return cudaErrorInvalidValue;
+    }
+    int g = rows_pairs_per_block(cols);
+    if (g > rows / 2) g = rows / 2;
+    const int log2g = ilog2(g);
+    switch (ilog2(rows)) {
+#define GBFFT_CASE(L) \
+    case L: return run_cols_analytic<(1 << L)>(spec, f, cols, nimg, log2g, tw_rows, s);
+        GBFFT_CASE(1) GBFFT_CASE(2) GBFFT_CASE(3) GBFFT_CASE(4) GBFFT_CASE(5) GBFFT_CASE(6) GBFFT_CASE(7)
+        GBFFT_CASE(8) GBFFT_CASE(9) GBFFT_CASE(10) GBFFT_CASE(11) GBFFT_CASE(12) GBFFT_CASE(13)
+#undef GBFFT_CASE
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 cudaError_t launch_cols_filter(void *spec, const float *hs, const float *beta, long long hs_img, long long beta_img,

@@ -54,12 +54,57 @@ __device__ __forceinline__ int slot_e(int t, int e, int log2g) {
 }
 
 // One block's share of the column pass: half-spectrum columns bx*W .. bx*W + W - 1
-// of one image.  spec: that image's half spectra [M/2][N] (slot order), hs /
-// beta: its prepared filter.
-template <int N, typename FFT = Fp32Fft>
-__device__ __forceinline__ void cols_body(float2 *spec, const float *__restrict__ hs, const float *__restrict__ beta,
-                                          int M, int log2g, const float2 *__restrict__ tw, int bx,
-                                          unsigned char *smraw, FFT fft = FFT()) {
+// of one image.  spec: that image's half spectra [M/2][N] (slot order), filt:
+// its filter (prepared arrays, or analytic).
+// Filter policies of the column pass: h(u, k) = s Hs[u][k] of column k (k = 0:
+// alpha) and b(u) = beta of the packed column, for the rows u = t + T e.
+// The prepared filter of rows_impl.cuh, read from global memory:
+struct PreparedFilter {
+    static constexpr bool EARLY = false;  // read after the forward transform (no registers held during it)
+    const float *hs, *beta;
+    int N;
+    __device__ __forceinline__ float h(int u, int k) const { return hs[(size_t)k * N + u]; }
+    __device__ __forceinline__ float b(int u) const { return beta[u]; }
+};
+
+// Analytic filters computed in the column pass (no filter array is read).
+// All three are even, H[-u][-k] = H[u][k], so Hs = H:
+//   kind 1, Gaussian:    exp(-|f|^2 / (2 sigma^2)), p = 1 / (2 sigma^2)
+//   kind 2, Butterworth: 1 / (1 + (|f|^2 / D0^2)^n), p = 1 / D0^2, order n
+//   kind 3, disc (Eq. filtro): 0 where (u - N/2)^2 + (k - M/2)^2 <= b^2, else 1; q = floor(b^2)
+// with |f|^2 = u~^2 + k~^2 over the wrapped bins (u~ = u for u < N/2, u - N above).
+struct AnalyticFilter {
+    static constexpr bool EARLY = true;  // computed while the column's loads are in flight
+    int kind, order, N, M;
+    float p, s;
+    int q;  // disc: floor(b^2) (the squared distances are integers)
+    __device__ __forceinline__ float H(int u, int k) const {
+        if (kind == 3) {
+            const int du = u - (N >> 1), dk = k - (M >> 1);
+            return du * du + dk * dk <= q ? 0.f : 1.f;
+        }
+        const int wu = u < (N >> 1) ? u : u - N, wk = k < (M >> 1) ? k : k - M;
+        const float r2 = (float)(wu * wu + wk * wk);  // exact below 2^24, one rounding above
+        if (kind == 1) return expf(-r2 * p);
+        // x^order by squaring (order 1..16), then the correctly rounded reciprocal
+        const float x1 = r2 * p, x2 = x1 * x1, x4 = x2 * x2, x8 = x4 * x4;
+        float y = (order & 1) ? x1 : 1.f;
+        if (order & 2) y *= x2;
+        if (order & 4) y *= x4;
+        if (order & 8) y *= x8;
+        if (order & 16) y *= x8 * x8;
+        return __frcp_rn(1.f + y);
+    }
+    __device__ __forceinline__ float h(int u, int k) const {
+        if (k != 0) return s * H(u, k);
+        return 0.5f * s * (H(u, 0) + H(u, M >> 1));
+    }
+    __device__ __forceinline__ float b(int u) const { return 0.5f * s * (H(u, 0) - H(u, M >> 1)); }
+};
+
+template <int N, typename FFT = Fp32Fft, typename FILT = PreparedFilter>
+__device__ __forceinline__ void cols_body(float2 *spec, FILT filt, int M, int log2g, const float2 *__restrict__ tw,
+                                          int bx, unsigned char *smraw, FFT fft = FFT()) {
     typedef ColCfg<N> K;
     constexpr int E = K::E, T = K::T, W = K::W;
     const int w = threadIdx.x / T;
@@ -70,18 +115,23 @@ __device__ __forceinline__ void cols_body(float2 *spec, const float *__restrict_
     const bool active = k0 < half;  // narrow spectra: surplus column groups idle
     const int k = active ? k0 : 0;
     float2 *col = spec + (size_t)k * N;
-    const float *hcol = hs + (size_t)k * N;
 
     float2 v[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = active ? col[slot_e<N, E, T>(t, e, log2g)] : make_float2(0.f, 0.f);
 
+    float h[E];
+    if constexpr (FILT::EARLY) {
+#pragma unroll
+        for (int e = 0; e < E; ++e) h[e] = filt.h(t + T * e, k);
+    }
+
     fft.template run<N, E, -1>(v, ex, tw, t);
 
-    // the filter is read after the forward transform so it holds no registers during it
-    float h[E];
+    if constexpr (!FILT::EARLY) {
 #pragma unroll
-    for (int e = 0; e < E; ++e) h[e] = hcol[t + T * e];  // the prepared filter is in row order
+        for (int e = 0; e < E; ++e) h[e] = filt.h(t + T * e, k);
+    }
 
     if (bx == 0) {  // the group of column 0 needs Q[-u] (uniform per block)
         __syncthreads();
@@ -93,12 +143,11 @@ __device__ __forceinline__ void cols_body(float2 *spec, const float *__restrict_
 #pragma unroll
         for (int e = 0; e < E; ++e) v[e] = cscale(v[e], h[e]);
     } else {
-        const float *bcol = beta;
 #pragma unroll
         for (int e = 0; e < E; ++e) {
             const int u = t + T * e;
             const float2 qm = ex[pad16((N - u) & (N - 1))];
-            const float bt = bcol[u];
+            const float bt = filt.b(u);
             v[e] = make_float2(h[e] * v[e].x + bt * qm.x, h[e] * v[e].y - bt * qm.y);
         }
     }

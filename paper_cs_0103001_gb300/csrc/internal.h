@@ -72,6 +72,11 @@ cudaError_t launch_rows_fwd(const float *img, void *spec, int rows, int cols, in
 // hs + i * hs_img, beta + i * beta_img.
 cudaError_t launch_filter_prep(const float *H, float *hs, float *beta, int rows, int cols, int nimg, float scale,
                                long long h_stride, long long hs_img, long long beta_img, cudaStream_t s);
+// Column pass with an analytic filter computed in the kernel (no filter
+// array): kind 1 Gaussian (p0 = sigma in bins), 2 Butterworth (p0 = order,
+// p1 = cutoff D0 in bins), 3 disc of Eq. filtro (p0 = radius b); cols_impl.cuh.
+cudaError_t launch_cols_analytic(void *spec, int kind, double p0, double p1, int rows, int cols, int nimg,
+                                 const void *tw_rows, cudaStream_t s);
 // hs_img / beta_img: elements between images' prepared filters (0 = shared)
 cudaError_t launch_cols_filter(void *spec, const float *hs, const float *beta, long long hs_img, long long beta_img,
                                int rows, int cols, int nimg, const void *tw_rows, cudaStream_t s);

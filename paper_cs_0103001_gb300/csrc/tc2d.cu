@@ -53,8 +53,8 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, 2)
     extern __shared__ __align__(16) unsigned char smraw[];
     const size_t y = blockIdx.y;
     TcFft<TERMS> f = make_tc<ColCfg<N>::THREADS, TERMS>(smraw, ColCfg<N>::SMEM);
-    cols_body<N, TcFft<TERMS>>(spec + y * (M / 2) * N, hs + y * hs_img, beta + y * beta_img, M, log2g, tw,
-                               blockIdx.x, smraw, f);
+    cols_body<N, TcFft<TERMS>>(spec + y * (M / 2) * N, PreparedFilter{hs + y * hs_img, beta + y * beta_img, N}, M,
+                               log2g, tw, blockIdx.x, smraw, f);
 }
 
 bool tc_supported(int rows, int cols) {

@@ -119,3 +119,12 @@ def test_padded_and_spectrum_entry_checks(nat):
     assert nat.lib.fft2_filter_ifft2_padded(h, fake, 460, 506, fake, fake, None) == nat.ERR_WORKSPACE
     assert nat.lib.fft2_spectrum(h, fake, 460, 506, fake, None) == nat.ERR_WORKSPACE
     assert nat.lib.fft_plan_destroy(h) == nat.OK
+
+
+def test_analytic_entry_checks(nat):
+    fake = ctypes.c_void_p(1 << 20)
+    assert nat.lib.fft2_filter_ifft2_analytic(None, fake, nat.FILTER_GAUSSIAN, 3.0, 0.0, fake, None) == nat.ERR_NULL
+    h = ctypes.c_void_p()
+    assert nat.lib.fft2_plan_create(64, 64, 1, 1, ctypes.byref(h)) == nat.OK
+    assert nat.lib.fft2_filter_ifft2_analytic(h, fake, nat.FILTER_GAUSSIAN, 3.0, 0.0, fake, None) == nat.ERR_WORKSPACE
+    assert nat.lib.fft_plan_destroy(h) == nat.OK
