@@ -74,8 +74,8 @@ STAGE_SOURCES = {
     "filter_prep": ("rows.cu", "rows_impl.cuh", "fft_core.cuh", "layout.cuh"),
     "cols_filter": ("cols.cu", "cols_impl.cuh", "fft_core.cuh", "layout.cuh"),
     "onchip": ("onchip.cu", "fft_core.cuh", "layout.cuh"),
-    "fourstep_a": ("fourstep.cu", "fft_core.cuh"),
-    "fourstep_b": ("fourstep.cu", "fft_core.cuh"),
+    "fourstep_a": ("fourstep.cu", "fft_core.cuh", "tma.cuh"),
+    "fourstep_b": ("fourstep.cu", "fft_core.cuh", "tma.cuh"),
     "fft1d_cluster": ("fft1d_cluster.cu", "fft_core.cuh"),
 }
 

@@ -299,6 +299,13 @@ int gbfft_last_cuda_error(void);
  * launches[0..nstages) (either may be NULL), then forget the records. */
 int gbfft_plan_profile_read(gbfft_plan_t plan, double *ms, int64_t *launches, int nstages);
 
+/* Read and clear the plan's device status word (synchronous: waits for the
+ * plan's work on the device).  Kernels that wait on asynchronous copies (the
+ * TMA-staged four-step pass of 1D complex64 plans) wait a bounded time; one
+ * that gives up leaves its outputs unwritten and records it here:
+ * GBFFT_ERR_TIMEOUT.  GBFFT_OK otherwise. */
+int gbfft_device_status(gbfft_plan_t plan);
+
 /* Library version as 10000*major + 100*minor + patch. */
 int gbfft_version(void);
 

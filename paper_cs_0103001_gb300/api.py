@@ -60,6 +60,10 @@ class _PlanBase:
     def set_option(self, key: int, value: int) -> None:
         nat.call("fft_plan_set_option", self.handle, int(key), int(value))
 
+    def device_status(self) -> None:
+        """Raise if a kernel of this plan gave up a bounded wait (synchronous)."""
+        nat.call("gbfft_device_status", self.handle)
+
     def profile_read(self) -> dict[str, tuple[float, int]]:
         n = len(nat.STAGES)
         ms = (ctypes.c_double * n)()

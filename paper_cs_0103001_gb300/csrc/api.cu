@@ -51,6 +51,7 @@ struct gbfft_plan {
     bool bound = false;
     // layout (byte offsets into ws)
     size_t off_tw0 = 0, off_tw1 = 0, off_tw2 = 0, off_tw3 = 0, off_buf = 0, off_buf2 = 0, need = 0;
+    size_t off_status = 0;  // device status word (bounded waits that gave up)
     size_t off_hs = 0, off_beta = 0, off_grad = 0;  // 2D: prepared filter, beta, adjoint sums
     int64_t chunk = 0;           // transforms (1D four-step) or images (2D) per workspace chunk
     int fs_l1 = 0, fs_l2 = 0;    // four-step split
@@ -109,6 +110,8 @@ void layout_batched(gbfft_plan *p) {
         im.beta_off = (long long)off;
         off = align_up(off + (size_t)im.rows * 4);
     }
+    p->off_status = align_up(off);
+    off = p->off_status + kAlign;
     p->need = off;
 }
 
@@ -185,6 +188,8 @@ void layout(gbfft_plan *p) {
             off = align_up(off + (size_t)(cols / 2 + 1) * rows * 4);
         }
     }
+    p->off_status = align_up(off);
+    off = p->off_status + kAlign;
     p->need = off;
 }
 
@@ -248,7 +253,7 @@ int run_1d(gbfft_plan *p, const void *in, void *out, int dir, cudaStream_t s) {
         char *dst = static_cast<char *>(out) + (size_t)b0 * n * cs;
         rc = launch(p, GBFFT_STAGE_FOURSTEP_A, s, [&] {
             return launch_fourstep_a(src, p->ws + p->off_buf, p->log2n, nb, dbl, dir, p->ws + p->off_tw0,
-                                     p->ws + p->off_tw2, s);
+                                     p->ws + p->off_tw2, reinterpret_cast<int *>(p->ws + p->off_status), s);
         });
         if (rc) return rc;
         rc = launch(p, GBFFT_STAGE_FOURSTEP_B, s, [&] {
@@ -422,6 +427,10 @@ int fft_plan_bind_workspace(gbfft_plan_t p, void *workspace, size_t bytes, gbfft
     p->bound = false;
     const bool dbl = is_dbl(p);
     int rc;
+    {
+        cudaError_t e = cudaMemsetAsync(p->ws + p->off_status, 0, sizeof(int), s);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
     if (p->kind == KIND_1D) {
         if (p->log2n <= max_single_log2(p)) {
             rc = launch(p, GBFFT_STAGE_TWIDDLES, s, [&] { return launch_twiddles(p->ws + p->off_tw0, 1 << p->log2n, dbl, s); });
@@ -905,6 +914,16 @@ int fft_plan_get_option(gbfft_plan_t p, int key, int64_t *value) {
         case GBFFT_OPT_ONCHIP: *value = p->opt_onchip; return GBFFT_OK;
         default: return GBFFT_ERR_INVALID_VALUE;
     }
+}
+
+int gbfft_device_status(gbfft_plan_t p) {
+    int rc = check_plan_ready(p);
+    if (rc) return rc;
+    int word = 0;
+    cudaError_t e = cudaMemcpy(&word, p->ws + p->off_status, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && word != 0) e = cudaMemset(p->ws + p->off_status, 0, sizeof(int));
+    if (e != cudaSuccess) return cuda_fail(e);
+    return word ? GBFFT_ERR_TIMEOUT : GBFFT_OK;
 }
 
 int fft_plan_destroy(gbfft_plan_t p) {

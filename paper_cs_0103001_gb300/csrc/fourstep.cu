@@ -13,8 +13,11 @@
 // tile of W adjacent columns (pass A) or rows (pass B) per thread block so
 // every global access is a run of W or 32/W contiguous elements.  The
 // intermediate goes to a workspace chunk sized to stay in L2 when it can.
+#include <cuda.h>
+
 #include "fft_core.cuh"
 #include "internal.h"
+#include "tma.cuh"
 
 #ifndef GBFFT_FS_BIGN
 #define GBFFT_FS_BIGN 4096  // fp32 factor lengths from which a block has 1024 threads
@@ -80,6 +83,58 @@ __global__ void __launch_bounds__(FsCfg<N, R>::MAXT, FsCfg<N, R>::MINB)
     }
 }
 
+// Pass A for complex64 with its tile staged by the TMA: one thread loads the
+// block's N1 x W tile (W adjacent columns, row pitch n2) as boxes of up to
+// 256 rows into shared memory; the block waits on an mbarrier (bounded: a
+// wait that gives up sets *status and the block leaves), reads its elements
+// from the dense tile, and the transform reuses the same memory as its
+// exchange buffer.  Twiddle and store as k_fourstep_a.
+template <int N, int DIR>
+__global__ void __launch_bounds__(FsCfg<N, float>::MAXT, FsCfg<N, float>::MINB)
+    k_fourstep_a_tma(const __grid_constant__ CUtensorMap map, float2 *tmp, int log2n2,
+                     const float2 *__restrict__ tw, const float2 *__restrict__ t4, int log2f, int *status) {
+    typedef FsCfg<N, float> K;
+    constexpr int E = K::E, T = K::T, W = K::WMAX, BR = N < 256 ? N : 256;
+    constexpr size_t EXCH_BYTES = (size_t)padded_len(N) * W * sizeof(float2);
+    extern __shared__ __align__(128) unsigned char smraw[];
+    unsigned char *base = smraw + ((128u - (smem_u32(smraw) & 127u)) & 127u);  // TMA wants 128-byte alignment
+    float2 *sm = reinterpret_cast<float2 *>(base);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(base + EXCH_BYTES);
+    int *ok = reinterpret_cast<int *>(base + EXCH_BYTES + 8);
+    const int w = threadIdx.x % W;
+    const int t = threadIdx.x / W;
+    const int j2 = blockIdx.x * W + w;
+    if (threadIdx.x == 0) mbar_init(bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(bar, (uint32_t)(N * W * sizeof(float2)));
+        for (int r = 0; r < N; r += BR) tma_load_3d(sm + r * W, &map, 2 * blockIdx.x * W, r, blockIdx.y, bar);
+        int done = mbar_wait_bounded(bar, 0, kTmaPolls) ? 1 : 0;
+        if (!done) {
+            atomicExch(status, 1);
+            mbar_wait_bounded(bar, 0, kTmaPolls);  // one more bounded wait for the copies in flight
+        }
+        *ok = done;
+    }
+    __syncthreads();
+    if (!*ok) return;  // uniform per block
+    const size_t base_g = (size_t)blockIdx.y * ((size_t)N << log2n2) + j2;
+    float2 v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = sm[(t + T * e) * W + w];
+    // fft_regs starts its first exchange with a block barrier, after every
+    // thread read its elements from the tile
+    static_assert(RadixPlan<N>::P >= 2, "at least one exchange");
+    fft_regs<N, E, DIR>(v, sm + w, tw, t, W);
+#pragma unroll
+    for (int e = 0; e < E; ++e) {
+        const int k1 = t + T * e;
+        const float2 f = tw_two_level(t4, k1 * j2, log2f);
+        v[e] = DIR < 0 ? cmul(v[e], f) : cmulc(v[e], f);
+        tmp[base_g + ((size_t)k1 << log2n2)] = v[e];
+    }
+}
+
 // Pass B: row transforms of length N2 (= N) over the n1 x N2 view, stored at k1 + n1 k2.
 template <int N, int DIR, typename R>
 __global__ void __launch_bounds__(FsCfg<N, R>::MAXT, FsCfg<N, R>::MINB)
@@ -104,9 +159,67 @@ __global__ void __launch_bounds__(FsCfg<N, R>::MAXT, FsCfg<N, R>::MINB)
     for (int e = 0; e < E; ++e) dst[(size_t)(t + T * e) << log2n1] = cscale(v[e], scale);
 }
 
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled from the driver (looked up once; null if unavailable)
+static EncodeTiledFn encode_tiled() {
+    static const EncodeTiledFn fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return (EncodeTiledFn) nullptr;
+        }
+        return reinterpret_cast<EncodeTiledFn>(p);
+    }();
+    return fn;
+}
+
+template <int N, typename R>
+static cudaError_t run_a_tma(const void *in, void *tmp, int log2n2, long long nb, int dir, const void *tw,
+                             const void *t4, int log2f, int *status, cudaStream_t s, bool *used) {
+    *used = false;
+    if constexpr (sizeof(R) != 4) {
+        return cudaSuccess;
+    } else {
+        typedef FsCfg<N, float> K;
+        constexpr int W = K::WMAX, BR = N < 256 ? N : 256;
+        const EncodeTiledFn enc = encode_tiled();
+        if (!enc || !status) return cudaSuccess;
+        // the chunk as a 3D float tensor: {2 n2 (re, im of each column), N1 rows, nb transforms}
+        const cuuint64_t n2 = 1ull << log2n2;
+        cuuint64_t dims[3] = {2 * n2, (cuuint64_t)N, (cuuint64_t)nb};
+        cuuint64_t strides[2] = {2 * n2 * sizeof(float), (cuuint64_t)N * 2 * n2 * sizeof(float)};
+        cuuint32_t box[3] = {2 * W, BR, 1};
+        cuuint32_t estr[3] = {1, 1, 1};
+        CUtensorMap map;
+        if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(in), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaSuccess;  // not encodable here: the caller runs the plain kernel
+        const size_t smem = (size_t)padded_len(N) * W * sizeof(float2) + 16 + 128;
+        auto kern = dir < 0 ? k_fourstep_a_tma<N, -1> : k_fourstep_a_tma<N, 1>;
+        cudaError_t e = set_smem_attrs((const void *)kern, smem, K::MINB);
+        if (e != cudaSuccess) return e;
+        dim3 grid((1 << log2n2) / W, (unsigned)nb);
+        kern<<<grid, W * K::T, smem, s>>>(map, static_cast<float2 *>(tmp), log2n2, static_cast<const float2 *>(tw),
+                                          static_cast<const float2 *>(t4), log2f, status);
+        *used = true;
+        return cudaGetLastError();
+    }
+}
+
 template <int N, typename R>
 static cudaError_t run_a(const void *in, void *tmp, int log2n2, long long nb, int dir, const void *tw,
-                         const void *t4, int log2f, cudaStream_t s) {
+                         const void *t4, int log2f, int *status, cudaStream_t s) {
+    if (nb > 65535) return cudaErrorInvalidConfiguration;
+    bool used = false;
+    cudaError_t te = run_a_tma<N, R>(in, tmp, log2n2, nb, dir, tw, t4, log2f, status, s, &used);
+    if (te != cudaSuccess || used) return te;
     typedef typename cvec<R>::type C;
     typedef FsCfg<N, R> K;
     constexpr int W = K::WMAX;  // <= 64 <= the other factor (>= 2^7)
@@ -143,10 +256,10 @@ static cudaError_t run_b(const void *tmp, void *out, int log2n1, long long nb, i
 
 template <typename R>
 static cudaError_t dispatch_a(const void *in, void *tmp, int l1, int l2, long long nb, int dir, const void *tw,
-                              const void *t4, int log2f, cudaStream_t s) {
+                              const void *t4, int log2f, int *status, cudaStream_t s) {
     switch (l1) {
 #define GBFFT_A(L) \
-    case L: return run_a<(1 << L), R>(in, tmp, l2, nb, dir, tw, t4, log2f, s);
+    case L: return run_a<(1 << L), R>(in, tmp, l2, nb, dir, tw, t4, log2f, status, s);
         GBFFT_FS_CASES(GBFFT_A)
 #undef GBFFT_A
         default: return cudaErrorInvalidValue;
@@ -166,12 +279,12 @@ static cudaError_t dispatch_b(const void *tmp, void *out, int l1, int l2, long l
 }
 
 cudaError_t launch_fourstep_a(const void *in, void *tmp, int log2n, long long batch, bool dbl, int dir,
-                              const void *tw_n1, const void *tw_4s, cudaStream_t s) {
+                              const void *tw_n1, const void *tw_4s, int *status, cudaStream_t s) {
     int l1, l2;
     fourstep_split(log2n, dbl, &l1, &l2);
     const int log2f = (log2n + 1) / 2;
-    return dbl ? dispatch_a<double>(in, tmp, l1, l2, batch, dir, tw_n1, tw_4s, log2f, s)
-               : dispatch_a<float>(in, tmp, l1, l2, batch, dir, tw_n1, tw_4s, log2f, s);
+    return dbl ? dispatch_a<double>(in, tmp, l1, l2, batch, dir, tw_n1, tw_4s, log2f, status, s)
+               : dispatch_a<float>(in, tmp, l1, l2, batch, dir, tw_n1, tw_4s, log2f, status, s);
 }
 
 cudaError_t launch_fourstep_b(const void *tmp, void *out, int log2n, long long batch, bool dbl, int dir,

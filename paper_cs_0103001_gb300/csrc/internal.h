@@ -45,7 +45,7 @@ cudaError_t launch_fft1d(const void *in, void *out, int log2n, long long batch, 
 //           out[k1 + n1*k2] (scaled by `scale`).
 int fourstep_split(int log2n, bool dbl, int *log2n1, int *log2n2);
 cudaError_t launch_fourstep_a(const void *in, void *tmp, int log2n, long long batch, bool dbl, int dir,
-                              const void *tw_n1, const void *tw_4s, cudaStream_t s);
+                              const void *tw_n1, const void *tw_4s, int *status, cudaStream_t s);
 cudaError_t launch_fourstep_b(const void *tmp, void *out, int log2n, long long batch, bool dbl, int dir,
                               const void *tw_n2, double scale, cudaStream_t s);
 

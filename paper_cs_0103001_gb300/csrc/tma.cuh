@@ -1,0 +1,65 @@
+// tma.cuh — tensor-memory-accelerator (TMA) tile loads with an mbarrier.
+//
+// One thread issues cp.async.bulk.tensor copies of a box of a tensor map
+// (encoded on the host, passed as a __grid_constant__ kernel parameter) into
+// shared memory; they signal an mbarrier with the bytes they deliver, and the
+// block waits on it.  The wait is bounded: it gives up after a fixed number
+// of polls, reports through a device status word and leaves the data alone.
+#pragma once
+
+#include <cuda.h>
+#include <stdint.h>
+
+namespace gbfft {
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+    // make the initialised barrier visible to the asynchronous (TMA) proxy
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+// Test the barrier's phase `parity` at most `polls` times (non-blocking tests,
+// a short sleep between them); true once it completed.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t polls) {
+    const uint32_t a = smem_u32(bar);
+    for (uint32_t i = 0; i < polls; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+        __nanosleep(64);
+    }
+    return false;
+}
+
+// Box of a 3D tensor map at coordinates (c0, c1, c2) -> shared memory dst
+// (128-byte aligned); completion counted on bar.  c0 * element size must be
+// a multiple of 16 bytes.
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int c0, int c1, int c2,
+                                            uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::
+            "r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// Tests of a bounded wait (each followed by a 64 ns sleep): the copies of one
+// tile take microseconds, so a wait this long (about a quarter second or
+// more) means they will not complete.
+constexpr uint32_t kTmaPolls = 1u << 22;
+
+}  // namespace gbfft

@@ -128,3 +128,11 @@ def test_analytic_entry_checks(nat):
     assert nat.lib.fft2_plan_create(64, 64, 1, 1, ctypes.byref(h)) == nat.OK
     assert nat.lib.fft2_filter_ifft2_analytic(h, fake, nat.FILTER_GAUSSIAN, 3.0, 0.0, fake, None) == nat.ERR_WORKSPACE
     assert nat.lib.fft_plan_destroy(h) == nat.OK
+
+
+def test_device_status_checks(nat):
+    assert nat.lib.gbfft_device_status(None) == nat.ERR_NULL
+    rc, h = _plan(nat, n=1 << 20, batch=1)
+    assert rc == nat.OK
+    assert nat.lib.gbfft_device_status(h) == nat.ERR_WORKSPACE  # nothing bound yet
+    assert nat.lib.fft_plan_destroy(h) == nat.OK

@@ -164,3 +164,21 @@ def test_cluster_path_against_oracle_and_four_step(gb, log2n, batch):
         assert np.array_equal(t.cpu().numpy(), f)
         outs[onchip] = f
     assert max_rel_l2(outs[1], outs[0], axes=-1) <= 2 * tol_fp32(n)
+
+
+@pytest.mark.parametrize("log2n,batch", [(18, 3), (20, 2), (22, 1), (24, 1)])
+def test_tma_four_step_and_device_status(gb, log2n, batch):
+    """Complex64 four-step lengths stage pass A's tiles with the TMA; results
+    match the oracle and the plan's device status word stays clear."""
+    import torch
+
+    n = 1 << log2n
+    x = synth.complex_uniform((batch, n), 4, log2n, batch)
+    xo = x.astype(np.complex128)
+    plan = gb.Plan1D(n, batch, torch.complex64, "cuda")
+    t = torch.from_numpy(x).cuda()
+    f = plan.forward(t).cpu().numpy()
+    b = plan.inverse(t).cpu().numpy()
+    plan.device_status()  # raises on a timed-out wait
+    assert max_rel_l2(f, oracle.fft(xo), axes=-1) <= tol_fp32(n)
+    assert max_rel_l2(b, oracle.ifft(xo), axes=-1) <= tol_fp32(n)
