@@ -394,7 +394,8 @@ def run_gbfft(args):
                             "copies per step with no compute (the host link's ceiling)"},
             "gpu_launches": int(round(launches_per_step * args.steps)),
             "variants": dict(run_variants(), pipeline4096_precision=_guard(lambda: variant_precision(img, H, ref, flush)),
-                             pipeline4096_analytic_filter=_guard(lambda: variant_analytic(img, flush)))
+                             pipeline4096_analytic_filter=_guard(lambda: variant_analytic(img, flush)),
+                             cufft_context=_guard(lambda: variant_cufft_context(img, H, ref, flush)))
             if args.variants else None,
             "clocks": clk,
             "wall_s_timed": round(wall, 4),
@@ -491,6 +492,37 @@ def variant_precision(img, H, ref, flush, steps: int = 100):
         got = out.cpu().numpy().astype(np.float64)
         res[name] = {"us": round(ms * 1e3, 2),
                      "rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref))}
+    return res
+
+
+def variant_cufft_context(img, H, ref, flush, steps: int = 100):
+    """Context only, never called by the library: the same 4096^2 workload
+    through torch.fft (cuFFT): rfft2 -> x H on the half spectrum -> irfft2
+    (equal to Re(ifft2(H . fft2(img))) for this even filter), and batched 1D
+    complex64 forward transforms of the fft1d sizes."""
+    import torch
+
+    Hh = H[:, : H.shape[1] // 2 + 1].contiguous()
+    res = {"note": "torch.fft (cuFFT) timed as context; not part of the library"}
+    out = {}
+
+    def pipe():
+        out["y"] = torch.fft.irfft2(torch.fft.rfft2(img, norm="forward") * Hh, s=tuple(img.shape), norm="forward")
+
+    ms = _timed(pipe, steps, 5, flush)
+    got = out["y"].cpu().numpy().astype(np.float64)
+    res["pipeline4096"] = {"us": round(ms * 1e3, 2), "rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref))}
+    del out["y"]
+    from paper_cs_0103001_gb300 import synth
+
+    for log2n in (12, 20, 24):
+        n = 1 << log2n
+        x = torch.from_numpy(synth.complex_uniform(((1 << 26) // n, n), 2, log2n)).cuda()
+        ms = _timed(lambda: torch.fft.fft(x, norm="forward"), 10, 3)
+        res[f"fft1d_c64_2^{log2n}"] = {"us": round(ms * 1e3, 1),
+                                       "gbs_one_pass": round(2 * x.numel() * 8 / (ms * 1e-3) / 1e9, 1)}
+        del x
+        torch.cuda.empty_cache()
     return res
 
 

@@ -50,7 +50,7 @@ struct gbfft_plan {
     size_t ws_bytes = 0;
     bool bound = false;
     // layout (byte offsets into ws)
-    size_t off_tw0 = 0, off_tw1 = 0, off_tw2 = 0, off_tw3 = 0, off_buf = 0, off_buf2 = 0, need = 0;
+    size_t off_tw0 = 0, off_tw1 = 0, off_tw2 = 0, off_tw3 = 0, off_tw5 = 0, off_buf = 0, off_buf2 = 0, need = 0;
     size_t off_status = 0;  // device status word (bounded waits that gave up)
     size_t off_hs = 0, off_beta = 0, off_grad = 0;  // 2D: prepared filter, beta, adjoint sums
     int64_t chunk = 0;           // transforms (1D four-step) or images (2D) per workspace chunk
@@ -140,6 +140,8 @@ void layout(gbfft_plan *p) {
             off = align_up(off + (size_t)n2 * csize(p));
             p->off_tw2 = off;
             off = align_up(off + (size_t)n4s * csize(p));
+            p->off_tw5 = off;  // coarse inter-pass table of pass A
+            off = align_up(off + (size_t)16 * n2 * csize(p));
             p->off_tw3 = off;  // full inter-pass table of the cluster path
             if (fft1d_cluster_supported(p->log2n, is_dbl(p))) off = align_up(off + (size_t)n * csize(p));
             p->off_buf = off;
@@ -253,7 +255,8 @@ int run_1d(gbfft_plan *p, const void *in, void *out, int dir, cudaStream_t s) {
         char *dst = static_cast<char *>(out) + (size_t)b0 * n * cs;
         rc = launch(p, GBFFT_STAGE_FOURSTEP_A, s, [&] {
             return launch_fourstep_a(src, p->ws + p->off_buf, p->log2n, nb, dbl, dir, p->ws + p->off_tw0,
-                                     p->ws + p->off_tw2, reinterpret_cast<int *>(p->ws + p->off_status), s);
+                                     p->ws + p->off_tw2, p->ws + p->off_tw5,
+                                     reinterpret_cast<int *>(p->ws + p->off_status), s);
         });
         if (rc) return rc;
         rc = launch(p, GBFFT_STAGE_FOURSTEP_B, s, [&] {
@@ -439,6 +442,7 @@ int fft_plan_bind_workspace(gbfft_plan_t p, void *workspace, size_t bytes, gbfft
                 cudaError_t e = launch_twiddles(p->ws + p->off_tw0, 1 << p->fs_l1, dbl, s);
                 if (e == cudaSuccess) e = launch_twiddles(p->ws + p->off_tw1, 1 << p->fs_l2, dbl, s);
                 if (e == cudaSuccess) e = launch_fourstep_twiddles(p->ws + p->off_tw2, 1 << p->log2n, dbl, s);
+                if (e == cudaSuccess) e = launch_fourstep_coarse_twiddles(p->ws + p->off_tw5, 1 << p->fs_l2, dbl, s);
                 if (e == cudaSuccess && fft1d_cluster_supported(p->log2n, dbl))
                     e = launch_fourstep_full_twiddles(p->ws + p->off_tw3, 1 << p->log2n, p->fs_l2, s);
                 return e;

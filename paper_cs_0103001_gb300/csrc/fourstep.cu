@@ -7,7 +7,11 @@
 //   j = j1 N2 + j2,  k = k1 + N1 k2,
 //   X[k1 + N1 k2] = sum_j2 W_N2^(j2 k2) [ W_N^(j2 k1) sum_j1 x[j1 N2 + j2] W_N1^(j1 k1) ].
 // Pass A runs the inner length-N1 transforms down the columns j2 of the
-// N1 x N2 row-major view and multiplies by W_N^(j2 k1) (two-level table);
+// N1 x N2 row-major view and multiplies by W_N^(j2 k1).  A thread holds rows
+// k1 = t + T e (T = N1/16, e < 16) of one column j2, so the factor splits as
+// W_N^(t j2) (once per thread, from the two-level table) times
+// W_N^(T e j2) = W_(16 N2)^(e j2) (a 16 x N2 table read along j2: adjacent
+// threads read adjacent entries);
 // pass B runs the outer length-N2 transforms along the rows k1 and stores
 // bin k2 of row k1 at k1 + N1 k2, the natural order of X.  Both passes move a
 // tile of W adjacent columns (pass A) or rows (pass B) per thread block so
@@ -60,7 +64,7 @@ template <int N, int DIR, typename R>
 __global__ void __launch_bounds__(FsCfg<N, R>::MAXT, FsCfg<N, R>::MINB)
     k_fourstep_a(const typename cvec<R>::type *in, typename cvec<R>::type *tmp, int log2n2,
                  const typename cvec<R>::type *__restrict__ tw, const typename cvec<R>::type *__restrict__ t4,
-                 int log2f) {
+                 int log2f, const typename cvec<R>::type *__restrict__ t5) {
     typedef typename cvec<R>::type C;
     typedef FsCfg<N, R> K;
     constexpr int E = K::E, T = K::T, W = K::WMAX;
@@ -74,10 +78,13 @@ __global__ void __launch_bounds__(FsCfg<N, R>::MAXT, FsCfg<N, R>::MINB)
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = in[base + ((size_t)(t + T * e) << log2n2)];
     fft_regs<N, E, DIR>(v, sm + w, tw, t, W);
+    static_assert(E == 16, "rows t + T e with T = N1 / 16");
+    const C a = tw_two_level(t4, t * j2, log2f);  // W_N^(t j2), t j2 < N / 16
+    const C *t5j = t5 + j2;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         const int k1 = t + T * e;
-        const C f = tw_two_level(t4, k1 * j2, log2f);  // k1 j2 < N1 n2: no reduction needed
+        const C f = cmul(a, __ldg(t5j + ((size_t)e << log2n2)));  // W_N^(k1 j2)
         v[e] = DIR < 0 ? cmul(v[e], f) : cmulc(v[e], f);
         tmp[base + ((size_t)k1 << log2n2)] = v[e];
     }
@@ -92,7 +99,8 @@ __global__ void __launch_bounds__(FsCfg<N, R>::MAXT, FsCfg<N, R>::MINB)
 template <int N, int DIR>
 __global__ void __launch_bounds__(FsCfg<N, float>::MAXT, FsCfg<N, float>::MINB)
     k_fourstep_a_tma(const __grid_constant__ CUtensorMap map, float2 *tmp, int log2n2,
-                     const float2 *__restrict__ tw, const float2 *__restrict__ t4, int log2f, int *status) {
+                     const float2 *__restrict__ tw, const float2 *__restrict__ t4, int log2f,
+                     const float2 *__restrict__ t5, int *status) {
     typedef FsCfg<N, float> K;
     constexpr int E = K::E, T = K::T, W = K::WMAX, BR = N < 256 ? N : 256;
     constexpr size_t EXCH_BYTES = (size_t)padded_len(N) * W * sizeof(float2);
@@ -126,10 +134,13 @@ __global__ void __launch_bounds__(FsCfg<N, float>::MAXT, FsCfg<N, float>::MINB)
     // thread read its elements from the tile
     static_assert(RadixPlan<N>::P >= 2, "at least one exchange");
     fft_regs<N, E, DIR>(v, sm + w, tw, t, W);
+    static_assert(E == 16, "rows t + T e with T = N1 / 16");
+    const float2 a = tw_two_level(t4, t * j2, log2f);
+    const float2 *t5j = t5 + j2;
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         const int k1 = t + T * e;
-        const float2 f = tw_two_level(t4, k1 * j2, log2f);
+        const float2 f = cmul(a, __ldg(t5j + ((size_t)e << log2n2)));
         v[e] = DIR < 0 ? cmul(v[e], f) : cmulc(v[e], f);
         tmp[base_g + ((size_t)k1 << log2n2)] = v[e];
     }
@@ -181,7 +192,7 @@ static EncodeTiledFn encode_tiled() {
 
 template <int N, typename R>
 static cudaError_t run_a_tma(const void *in, void *tmp, int log2n2, long long nb, int dir, const void *tw,
-                             const void *t4, int log2f, int *status, cudaStream_t s, bool *used) {
+                             const void *t4, int log2f, const void *t5, int *status, cudaStream_t s, bool *used) {
     *used = false;
     if constexpr (sizeof(R) != 4) {
         return cudaSuccess;
@@ -207,7 +218,8 @@ static cudaError_t run_a_tma(const void *in, void *tmp, int log2n2, long long nb
         if (e != cudaSuccess) return e;
         dim3 grid((1 << log2n2) / W, (unsigned)nb);
         kern<<<grid, W * K::T, smem, s>>>(map, static_cast<float2 *>(tmp), log2n2, static_cast<const float2 *>(tw),
-                                          static_cast<const float2 *>(t4), log2f, status);
+                                          static_cast<const float2 *>(t4), log2f, static_cast<const float2 *>(t5),
+                                          status);
         *used = true;
         return cudaGetLastError();
     }
@@ -215,10 +227,10 @@ static cudaError_t run_a_tma(const void *in, void *tmp, int log2n2, long long nb
 
 template <int N, typename R>
 static cudaError_t run_a(const void *in, void *tmp, int log2n2, long long nb, int dir, const void *tw,
-                         const void *t4, int log2f, int *status, cudaStream_t s) {
+                         const void *t4, int log2f, const void *t5, int *status, cudaStream_t s) {
     if (nb > 65535) return cudaErrorInvalidConfiguration;
     bool used = false;
-    cudaError_t te = run_a_tma<N, R>(in, tmp, log2n2, nb, dir, tw, t4, log2f, status, s, &used);
+    cudaError_t te = run_a_tma<N, R>(in, tmp, log2n2, nb, dir, tw, t4, log2f, t5, status, s, &used);
     if (te != cudaSuccess || used) return te;
     typedef typename cvec<R>::type C;
     typedef FsCfg<N, R> K;
@@ -230,7 +242,8 @@ static cudaError_t run_a(const void *in, void *tmp, int log2n2, long long nb, in
     if (nb > 65535) return cudaErrorInvalidConfiguration;
     dim3 grid((1 << log2n2) / W, (unsigned)nb);
     kern<<<grid, W * K::T, smem, s>>>(static_cast<const C *>(in), static_cast<C *>(tmp), log2n2,
-                                      static_cast<const C *>(tw), static_cast<const C *>(t4), log2f);
+                                      static_cast<const C *>(tw), static_cast<const C *>(t4), log2f,
+                                      static_cast<const C *>(t5));
     return cudaGetLastError();
 }
 
@@ -256,10 +269,10 @@ static cudaError_t run_b(const void *tmp, void *out, int log2n1, long long nb, i
 
 template <typename R>
 static cudaError_t dispatch_a(const void *in, void *tmp, int l1, int l2, long long nb, int dir, const void *tw,
-                              const void *t4, int log2f, int *status, cudaStream_t s) {
+                              const void *t4, int log2f, const void *t5, int *status, cudaStream_t s) {
     switch (l1) {
 #define GBFFT_A(L) \
-    case L: return run_a<(1 << L), R>(in, tmp, l2, nb, dir, tw, t4, log2f, status, s);
+    case L: return run_a<(1 << L), R>(in, tmp, l2, nb, dir, tw, t4, log2f, t5, status, s);
         GBFFT_FS_CASES(GBFFT_A)
 #undef GBFFT_A
         default: return cudaErrorInvalidValue;
@@ -279,12 +292,13 @@ static cudaError_t dispatch_b(const void *tmp, void *out, int l1, int l2, long l
 }
 
 cudaError_t launch_fourstep_a(const void *in, void *tmp, int log2n, long long batch, bool dbl, int dir,
-                              const void *tw_n1, const void *tw_4s, int *status, cudaStream_t s) {
+                              const void *tw_n1, const void *tw_4s, const void *tw_coarse, int *status,
+                              cudaStream_t s) {
     int l1, l2;
     fourstep_split(log2n, dbl, &l1, &l2);
     const int log2f = (log2n + 1) / 2;
-    return dbl ? dispatch_a<double>(in, tmp, l1, l2, batch, dir, tw_n1, tw_4s, log2f, status, s)
-               : dispatch_a<float>(in, tmp, l1, l2, batch, dir, tw_n1, tw_4s, log2f, status, s);
+    return dbl ? dispatch_a<double>(in, tmp, l1, l2, batch, dir, tw_n1, tw_4s, log2f, tw_coarse, status, s)
+               : dispatch_a<float>(in, tmp, l1, l2, batch, dir, tw_n1, tw_4s, log2f, tw_coarse, status, s);
 }
 
 cudaError_t launch_fourstep_b(const void *tmp, void *out, int log2n, long long batch, bool dbl, int dir,

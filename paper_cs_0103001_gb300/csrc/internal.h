@@ -35,6 +35,9 @@ cudaError_t launch_fft1d_cluster(const void *in, void *out, int log2n, long long
                                  const void *tw_n2, const void *tw_full, double scale, cudaStream_t s);
 // complex64 table [n1][n2] of W_n^(k1 j2), each rounded once from FP64
 cudaError_t launch_fourstep_full_twiddles(void *tw, int n, int log2n2, cudaStream_t s);
+// Coarse inter-pass table of the split n = n1 n2 (n1 >= 16): entry e * n2 + j2
+// holds W_(16 n2)^(e j2) = W_n^((n1/16) e j2), e < 16, j2 < n2.
+cudaError_t launch_fourstep_coarse_twiddles(void *tw, int n2, bool dbl, cudaStream_t s);
 cudaError_t launch_fft1d(const void *in, void *out, int log2n, long long batch, bool dbl, int dir,
                          const void *tw, double scale, cudaStream_t s);
 
@@ -44,8 +47,10 @@ cudaError_t launch_fft1d(const void *in, void *out, int log2n, long long batch, 
 //   pass B: for each k1, length-n2 DFT over j2 of tmp[k1*n2 + j2], written to
 //           out[k1 + n1*k2] (scaled by `scale`).
 int fourstep_split(int log2n, bool dbl, int *log2n1, int *log2n2);
+// tw_coarse: launch_fourstep_coarse_twiddles's table for n2.
 cudaError_t launch_fourstep_a(const void *in, void *tmp, int log2n, long long batch, bool dbl, int dir,
-                              const void *tw_n1, const void *tw_4s, int *status, cudaStream_t s);
+                              const void *tw_n1, const void *tw_4s, const void *tw_coarse, int *status,
+                              cudaStream_t s);
 cudaError_t launch_fourstep_b(const void *tmp, void *out, int log2n, long long batch, bool dbl, int dir,
                               const void *tw_n2, double scale, cudaStream_t s);
 

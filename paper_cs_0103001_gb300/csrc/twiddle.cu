@@ -54,6 +54,27 @@ __global__ void k_fourstep_full_twiddles(float2 *tw, int n, int log2n2) {
     tw[i] = make_float2((float)c, (float)s);
 }
 
+// Coarse inter-pass table: entry e * n2 + j2 holds W_(16 n2)^(e j2) (e j2 < 16 n2).
+template <typename C>
+__global__ void k_fourstep_coarse_twiddles(C *tw, int n2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 16 * n2) return;
+    const long long ph = (long long)(i / n2) * (i % n2);
+    double s, c;
+    sincospi(-2.0 * (double)ph / (16.0 * n2), &s, &c);
+    tw[i] = C{(decltype(tw[0].x))c, (decltype(tw[0].x))s};
+}
+
+cudaError_t launch_fourstep_coarse_twiddles(void *tw, int n2, bool dbl, cudaStream_t s) {
+    const int threads = 256;
+    const int blocks = (16 * n2 + threads - 1) / threads;
+    if (dbl)
+        k_fourstep_coarse_twiddles<double2><<<blocks, threads, 0, s>>>(static_cast<double2 *>(tw), n2);
+    else
+        k_fourstep_coarse_twiddles<float2><<<blocks, threads, 0, s>>>(static_cast<float2 *>(tw), n2);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_fourstep_full_twiddles(void *tw, int n, int log2n2, cudaStream_t s) {
     const int threads = 256;
     k_fourstep_full_twiddles<<<(n + threads - 1) / threads, threads, 0, s>>>(static_cast<float2 *>(tw), n, log2n2);
