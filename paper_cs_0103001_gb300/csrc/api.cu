@@ -260,7 +260,8 @@ int run_1d(gbfft_plan *p, const void *in, void *out, int dir, cudaStream_t s) {
         });
         if (rc) return rc;
         rc = launch(p, GBFFT_STAGE_FOURSTEP_B, s, [&] {
-            return launch_fourstep_b(p->ws + p->off_buf, dst, p->log2n, nb, dbl, dir, p->ws + p->off_tw1, scale, s);
+            return launch_fourstep_b(p->ws + p->off_buf, dst, p->log2n, nb, dbl, dir, p->ws + p->off_tw1, scale,
+                                     reinterpret_cast<int *>(p->ws + p->off_status), s);
         });
         if (rc) return rc;
     }

@@ -51,7 +51,9 @@ template <int L> struct ClCfg {
     static constexpr int CJ = N2 / C, CK = N1 / C;   // columns (A) and rows (B) per CTA
     static constexpr int TS = N1 + 1;                // tile row stride (odd: conflict-free)
     static constexpr int TILE = CJ * TS;
-    static constexpr int EXA = padded_len(N1) * WA, EXB = padded_len(N2) * WB;
+    // exchange layouts of the WA / WB interleaved transforms (fft_core.cuh)
+    static constexpr int PSA = exch_pad_shift<float2>(N1, WA), PSB = exch_pad_shift<float2>(N2, WB);
+    static constexpr int EXA = padded_len_ps<PSA>(N1) * WA, EXB = padded_len_ps<PSB>(N2) * WB;
     static constexpr int EXCH = EXA > EXB ? EXA : EXB;
     static constexpr size_t SMEM = (size_t)(TILE + EXCH) * sizeof(float2);
     static_assert(C >= 2 && C <= 16, "cluster size");
@@ -94,7 +96,7 @@ __global__ void __launch_bounds__(ClCfg<L>::THREADS, ClCfg<L>::MINB)
             // fft_regs starts its first exchange with a block barrier, so every
             // read of this round's columns is done before they are overwritten
             static_assert(RadixPlan<N1>::P >= 2, "at least one exchange");
-            fft_regs<N1, E, DIR>(v, exch + w, tw1, t, K::WA);
+            fft_regs<N1, E, DIR, K::PSA>(v, exch + w, tw1, t, K::WA);
 #pragma unroll
             for (int e = 0; e < E; ++e) {
                 const int k1 = t + K::T1 * e;
@@ -118,7 +120,7 @@ __global__ void __launch_bounds__(ClCfg<L>::THREADS, ClCfg<L>::MINB)
                 const float2 *src = cl.map_shared_rank(tile, j2 / K::CJ);
                 v[e] = src[(j2 % K::CJ) * TS + k1];
             }
-            fft_regs<N2, E, DIR>(v, exch + w, tw2, t, K::WB);
+            fft_regs<N2, E, DIR, K::PSB>(v, exch + w, tw2, t, K::WB);
 #pragma unroll
             for (int e = 0; e < E; ++e) y[(size_t)(t + K::T2 * e) * N1 + k1] = cscale(v[e], scale);
             __syncthreads();  // the exchange buffer is reused

@@ -44,6 +44,26 @@ __host__ __device__ constexpr int ilog2(long long n) { return n <= 1 ? 0 : 1 + i
 __device__ __forceinline__ int pad16(int x) { return x + (x >> 4); }
 __host__ __device__ constexpr int padded_len(int n) { return n + (n >> 4); }
 
+// The same with one pad slot per 2^PS elements (pad_ps<4> = pad16).
+template <int PS> __device__ __forceinline__ int pad_ps(int x) { return x + (x >> PS); }
+template <int PS> __host__ __device__ constexpr int padded_len_ps(int n) { return n + (n >> PS); }
+
+// Pad period for S transforms interleaved element by element (element x of
+// transform w at pad(x) * S + w, thread (t, w) = (tid / S, tid % S)).  A
+// shared-memory model of every exchange write and read (32 banks of 4 bytes;
+// 8-byte accesses served per half warp, 16-byte ones per quarter warp, one
+// wavefront per distinct word of the busiest bank; it reproduces the bank
+// conflicts measured on these kernels) gives the minimum with one pad per 16
+// elements for all lengths and interleaves used here except these, where the
+// threads t of a half warp would write the first pass's outputs (radix 2 or
+// 4, or the strided radix-16 writes at length 2048) to the same banks:
+//   complex64  length 512, S = 8: one pad per 2;  1024, S = 8: per 4;
+//              2048, S = 4: per 8;   complex128 length 2048, S = 4: per 8.
+template <typename C> __host__ __device__ constexpr int exch_pad_shift(int n, int s) {
+    return sizeof(C) == 8 ? (n == 512 && s == 8 ? 1 : n == 1024 && s == 8 ? 2 : n == 2048 && s == 4 ? 3 : 4)
+                          : (n == 2048 && s == 4 ? 3 : 4);
+}
+
 // ---------------------------------------------------------- radix plan --
 // Length N = 2^L.  N < 16: one pass of radix N.  Otherwise the first pass has
 // radix 2^(L mod 4) (16 when L mod 4 = 0) and every later pass radix 16.
@@ -218,7 +238,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // ------------------------------------------------------- one pass ---------
 // sm: this transform's exchange buffer, element x at sm[pad16(x) * S]
 // (S > 1 interleaves S transforms element by element).
-template <int N, int E, int R, int NS, int DIR, bool LAST, typename C>
+template <int N, int E, int R, int NS, int DIR, bool LAST, int PS, typename C>
 __device__ __forceinline__ void stockham_pass(C (&v)[E], C *sm, const C *__restrict__ tw, int t, int S) {
     constexpr int T = N / E;
     constexpr int Q = E / R;
@@ -248,21 +268,21 @@ __device__ __forceinline__ void stockham_pass(C (&v)[E], C *sm, const C *__restr
             const int j = t + q * T;
             const int base = (j / NS) * NS * R + (j & (NS - 1));
 #pragma unroll
-            for (int r = 0; r < R; ++r) sm[pad16(base + r * NS) * S] = v[q + r * Q];
+            for (int r = 0; r < R; ++r) sm[pad_ps<PS>(base + r * NS) * S] = v[q + r * Q];
         }
         __syncthreads();
 #pragma unroll
-        for (int e = 0; e < E; ++e) v[e] = sm[pad16(t + T * e) * S];
+        for (int e = 0; e < E; ++e) v[e] = sm[pad_ps<PS>(t + T * e) * S];
     }
 }
 
-template <int N, int E, int DIR, int P, typename C> struct Passes {
+template <int N, int E, int DIR, int P, int PS, typename C> struct Passes {
     __device__ __forceinline__ static void run(C (&v)[E], C *sm, const C *__restrict__ tw, int t, int S) {
         constexpr int NP = RadixPlan<N>::P;
         constexpr int R = RadixPlan<N>::radix(P);
         constexpr int NS = RadixPlan<N>::stride(P);
-        stockham_pass<N, E, R, NS, DIR, P == NP - 1>(v, sm, tw, t, S);
-        if constexpr (P + 1 < NP) Passes<N, E, DIR, P + 1, C>::run(v, sm, tw, t, S);
+        stockham_pass<N, E, R, NS, DIR, P == NP - 1, PS>(v, sm, tw, t, S);
+        if constexpr (P + 1 < NP) Passes<N, E, DIR, P + 1, PS, C>::run(v, sm, tw, t, S);
     }
 };
 
@@ -270,11 +290,11 @@ template <int N, int E, int DIR, int P, typename C> struct Passes {
 // T = N/E threads of one transform.  On entry and on exit v[e] is element /
 // bin t + T*e.  All threads of the block must call it (it contains
 // __syncthreads when N needs more than one pass).  Element x of the exchange
-// buffer is sm[pad16(x) * S]; S > 1 interleaves S transforms.
-template <int N, int E, int DIR, typename C>
+// buffer is sm[pad_ps<PS>(x) * S]; S > 1 interleaves S transforms.
+template <int N, int E, int DIR, int PS = 4, typename C>
 __device__ __forceinline__ void fft_regs(C (&v)[E], C *sm, const C *__restrict__ tw, int t, int S = 1) {
     static_assert(N % E == 0 && E >= RadixPlan<N>::MAXR, "bad elements per thread");
-    Passes<N, E, DIR, 0, C>::run(v, sm, tw, t, S);
+    Passes<N, E, DIR, 0, PS, C>::run(v, sm, tw, t, S);
 }
 
 }  // namespace gbfft

@@ -197,7 +197,7 @@ template <int N, int DIR, int TERMS, int P> struct PassesTC {
         if constexpr (R == 16) {
             tc_pass16<N, NS, DIR, TERMS>(v, sm, tw, t, S, st);
         } else {
-            stockham_pass<N, 16, R, NS, DIR, P == NP - 1>(v, sm, tw, t, S);
+            stockham_pass<N, 16, R, NS, DIR, P == NP - 1, 4>(v, sm, tw, t, S);
         }
         if constexpr (P + 1 < NP) PassesTC<N, DIR, TERMS, P + 1>::run(v, sm, tw, t, S, st);
     }

@@ -41,6 +41,18 @@ template <int N, typename R> struct FsCfg {
     static constexpr int SMEM_ELEMS = (sizeof(R) == 4 ? 16384 : 8192);
     static constexpr int W0 = SMEM_ELEMS / N < MAXT / T ? SMEM_ELEMS / N : MAXT / T;
     static constexpr int WMAX = W0 > 64 ? 64 : (W0 < 1 ? 1 : W0);
+    // exchange layout of the WMAX interleaved transforms (fft_core.cuh)
+    static constexpr int PS = exch_pad_shift<typename cvec<R>::type>(N, WMAX);
+    static constexpr int PL = padded_len_ps<PS>(N);
+};
+
+// Shared memory of k_fourstep_b_tma: the input tile (W rows of pitch N + 2),
+// the exchange buffer and the output box share one region.
+template <int N> struct FsTmaB {
+    typedef FsCfg<N, float> K;
+    static constexpr size_t TILE = (size_t)K::WMAX * (N + 2), EXCH = (size_t)K::PL * K::WMAX;
+    static constexpr size_t REGION_BYTES = (TILE > EXCH ? TILE : EXCH) * sizeof(float2);
+    static constexpr size_t SMEM = REGION_BYTES + 16 + 128;  // + mbarrier and flag, + alignment slack
 };
 
 int fourstep_split(int log2n, bool dbl, int *log2n1, int *log2n2) {
@@ -77,7 +89,7 @@ __global__ void __launch_bounds__(FsCfg<N, R>::MAXT, FsCfg<N, R>::MINB)
     C v[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = in[base + ((size_t)(t + T * e) << log2n2)];
-    fft_regs<N, E, DIR>(v, sm + w, tw, t, W);
+    fft_regs<N, E, DIR, K::PS>(v, sm + w, tw, t, W);
     static_assert(E == 16, "rows t + T e with T = N1 / 16");
     const C a = tw_two_level(t4, t * j2, log2f);  // W_N^(t j2), t j2 < N / 16
     const C *t5j = t5 + j2;
@@ -90,20 +102,22 @@ __global__ void __launch_bounds__(FsCfg<N, R>::MAXT, FsCfg<N, R>::MINB)
     }
 }
 
-// Pass A for complex64 with its tile staged by the TMA: one thread loads the
+// Pass A for complex64 with its tile moved by the TMA: one thread loads the
 // block's N1 x W tile (W adjacent columns, row pitch n2) as boxes of up to
 // 256 rows into shared memory; the block waits on an mbarrier (bounded: a
 // wait that gives up sets *status and the block leaves), reads its elements
 // from the dense tile, and the transform reuses the same memory as its
-// exchange buffer.  Twiddle and store as k_fourstep_a.
-template <int N, int DIR>
+// exchange buffer.  Twiddle as k_fourstep_a; with TSTORE the results go back
+// into the dense tile and leave by tensor stores through tmap (the same
+// geometry over the intermediate), else by plain stores.
+template <int N, int DIR, bool TSTORE>
 __global__ void __launch_bounds__(FsCfg<N, float>::MAXT, FsCfg<N, float>::MINB)
-    k_fourstep_a_tma(const __grid_constant__ CUtensorMap map, float2 *tmp, int log2n2,
-                     const float2 *__restrict__ tw, const float2 *__restrict__ t4, int log2f,
+    k_fourstep_a_tma(const __grid_constant__ CUtensorMap map, const __grid_constant__ CUtensorMap tmap, float2 *tmp,
+                     int log2n2, const float2 *__restrict__ tw, const float2 *__restrict__ t4, int log2f,
                      const float2 *__restrict__ t5, int *status) {
     typedef FsCfg<N, float> K;
     constexpr int E = K::E, T = K::T, W = K::WMAX, BR = N < 256 ? N : 256;
-    constexpr size_t EXCH_BYTES = (size_t)padded_len(N) * W * sizeof(float2);
+    constexpr size_t EXCH_BYTES = (size_t)K::PL * W * sizeof(float2);
     extern __shared__ __align__(128) unsigned char smraw[];
     unsigned char *base = smraw + ((128u - (smem_u32(smraw) & 127u)) & 127u);  // TMA wants 128-byte alignment
     float2 *sm = reinterpret_cast<float2 *>(base);
@@ -133,16 +147,29 @@ __global__ void __launch_bounds__(FsCfg<N, float>::MAXT, FsCfg<N, float>::MINB)
     // fft_regs starts its first exchange with a block barrier, after every
     // thread read its elements from the tile
     static_assert(RadixPlan<N>::P >= 2, "at least one exchange");
-    fft_regs<N, E, DIR>(v, sm + w, tw, t, W);
+    fft_regs<N, E, DIR, K::PS>(v, sm + w, tw, t, W);
     static_assert(E == 16, "rows t + T e with T = N1 / 16");
     const float2 a = tw_two_level(t4, t * j2, log2f);
     const float2 *t5j = t5 + j2;
+    if constexpr (TSTORE) __syncthreads();  // the last exchange's reads are complete
 #pragma unroll
     for (int e = 0; e < E; ++e) {
         const int k1 = t + T * e;
         const float2 f = cmul(a, __ldg(t5j + ((size_t)e << log2n2)));
         v[e] = DIR < 0 ? cmul(v[e], f) : cmulc(v[e], f);
-        tmp[base_g + ((size_t)k1 << log2n2)] = v[e];
+        if constexpr (TSTORE)
+            sm[k1 * W + w] = v[e];
+        else
+            tmp[base_g + ((size_t)k1 << log2n2)] = v[e];
+    }
+    if constexpr (TSTORE) {
+        fence_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int r = 0; r < N; r += BR) tma_store_3d(&tmap, 2 * blockIdx.x * W, r, blockIdx.y, sm + r * W);
+            bulk_commit();
+            bulk_wait_read();
+        }
     }
 }
 
@@ -164,10 +191,63 @@ __global__ void __launch_bounds__(FsCfg<N, R>::MAXT, FsCfg<N, R>::MINB)
     C v[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = row[t + T * e];
-    fft_regs<N, E, DIR>(v, sm + w, tw, t, W);
+    fft_regs<N, E, DIR, K::PS>(v, sm + w, tw, t, W);
     C *dst = out + img + k1;
 #pragma unroll
     for (int e = 0; e < E; ++e) dst[(size_t)(t + T * e) << log2n1] = cscale(v[e], scale);
+}
+
+// Pass B for complex64 through the TMA: the block's W rows k1 (contiguous in
+// the intermediate) arrive by bulk copies into rows of pitch N + 2 (so the
+// W threads that read one column of the tile hit different banks), with a
+// bounded mbarrier wait as in k_fourstep_a_tma; the transform reuses the
+// memory as its exchange buffer; the scaled outputs go back into it as the
+// dense box [k2][W] (W adjacent k1 of every row k2 of the n1-wide output
+// view) and leave by tensor stores.
+template <int N, int DIR>
+__global__ void __launch_bounds__(FsCfg<N, float>::MAXT, FsCfg<N, float>::MINB)
+    k_fourstep_b_tma(const float2 *tmp, const __grid_constant__ CUtensorMap omap, int log2n1,
+                     const float2 *__restrict__ tw, float scale, int *status) {
+    typedef FsCfg<N, float> K;
+    constexpr int E = K::E, T = K::T, W = K::WMAX, BR = N < 256 ? N : 256, RP = N + 2;
+    extern __shared__ __align__(128) unsigned char smraw[];
+    unsigned char *base = smraw + ((128u - (smem_u32(smraw) & 127u)) & 127u);
+    float2 *sm = reinterpret_cast<float2 *>(base);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(base + FsTmaB<N>::REGION_BYTES);
+    int *ok = reinterpret_cast<int *>(base + FsTmaB<N>::REGION_BYTES + 8);
+    const int w = threadIdx.x % W;
+    const int t = threadIdx.x / W;
+    const int k10 = blockIdx.x * W;
+    if (threadIdx.x == 0) mbar_init(bar, 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(bar, (uint32_t)(N * W * sizeof(float2)));
+        const float2 *src = tmp + (size_t)blockIdx.y * ((size_t)N << log2n1) + (size_t)k10 * N;
+        for (int r = 0; r < W; ++r) bulk_load(sm + r * RP, src + (size_t)r * N, N * sizeof(float2), bar);
+        int done = mbar_wait_bounded(bar, 0, kTmaPolls) ? 1 : 0;
+        if (!done) {
+            atomicExch(status, 1);
+            mbar_wait_bounded(bar, 0, kTmaPolls);  // one more bounded wait for the copies in flight
+        }
+        *ok = done;
+    }
+    __syncthreads();
+    if (!*ok) return;  // uniform per block
+    float2 v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = sm[w * RP + t + T * e];
+    static_assert(RadixPlan<N>::P >= 2, "at least one exchange");
+    fft_regs<N, E, DIR, K::PS>(v, sm + w, tw, t, W);
+    __syncthreads();  // the last exchange's reads are complete
+#pragma unroll
+    for (int e = 0; e < E; ++e) sm[(t + T * e) * W + w] = cscale(v[e], scale);
+    fence_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int r = 0; r < N; r += BR) tma_store_3d(&omap, 2 * k10, r, blockIdx.y, sm + r * W);
+        bulk_commit();
+        bulk_wait_read();
+    }
 }
 
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -207,17 +287,23 @@ static cudaError_t run_a_tma(const void *in, void *tmp, int log2n2, long long nb
         cuuint64_t strides[2] = {2 * n2 * sizeof(float), (cuuint64_t)N * 2 * n2 * sizeof(float)};
         cuuint32_t box[3] = {2 * W, BR, 1};
         cuuint32_t estr[3] = {1, 1, 1};
-        CUtensorMap map;
+        CUtensorMap map, tmap;
         if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(in), dims, strides, box, estr,
                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
+            enc(&tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, tmp, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                 CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
             return cudaSuccess;  // not encodable here: the caller runs the plain kernel
-        const size_t smem = (size_t)padded_len(N) * W * sizeof(float2) + 16 + 128;
-        auto kern = dir < 0 ? k_fourstep_a_tma<N, -1> : k_fourstep_a_tma<N, 1>;
+        const size_t smem = (size_t)K::PL * W * sizeof(float2) + 16 + 128;
+        // tensor stores when two blocks share an SM: the block holds its shared
+        // memory until the stores have read it, and the other block covers that
+        auto kern = K::MINB >= 2 ? (dir < 0 ? k_fourstep_a_tma<N, -1, true> : k_fourstep_a_tma<N, 1, true>)
+                                 : (dir < 0 ? k_fourstep_a_tma<N, -1, false> : k_fourstep_a_tma<N, 1, false>);
         cudaError_t e = set_smem_attrs((const void *)kern, smem, K::MINB);
         if (e != cudaSuccess) return e;
         dim3 grid((1 << log2n2) / W, (unsigned)nb);
-        kern<<<grid, W * K::T, smem, s>>>(map, static_cast<float2 *>(tmp), log2n2, static_cast<const float2 *>(tw),
+        kern<<<grid, W * K::T, smem, s>>>(map, tmap, static_cast<float2 *>(tmp), log2n2, static_cast<const float2 *>(tw),
                                           static_cast<const float2 *>(t4), log2f, static_cast<const float2 *>(t5),
                                           status);
         *used = true;
@@ -235,7 +321,7 @@ static cudaError_t run_a(const void *in, void *tmp, int log2n2, long long nb, in
     typedef typename cvec<R>::type C;
     typedef FsCfg<N, R> K;
     constexpr int W = K::WMAX;  // <= 64 <= the other factor (>= 2^7)
-    const size_t smem = (size_t)padded_len(N) * W * sizeof(C);
+    const size_t smem = (size_t)K::PL * W * sizeof(C);
     auto kern = dir < 0 ? k_fourstep_a<N, -1, R> : k_fourstep_a<N, 1, R>;
     cudaError_t e = set_smem_attrs((const void *)kern, smem, K::MINB);
     if (e != cudaSuccess) return e;
@@ -248,12 +334,51 @@ static cudaError_t run_a(const void *in, void *tmp, int log2n2, long long nb, in
 }
 
 template <int N, typename R>
+static cudaError_t run_b_tma(const void *tmp, void *out, int log2n1, long long nb, int dir, const void *tw,
+                             double scale, int *status, cudaStream_t s, bool *used) {
+    *used = false;
+    if constexpr (sizeof(R) != 4 || FsCfg<N, float>::MINB < 2) {
+        // one block per SM: it would idle while its tensor stores drain
+        return cudaSuccess;
+    } else {
+        typedef FsCfg<N, float> K;
+        constexpr int W = K::WMAX, BR = N < 256 ? N : 256;
+        const EncodeTiledFn enc = encode_tiled();
+        if (!enc || !status) return cudaSuccess;
+        // the output as a 3D float tensor: {2 n1 (re, im of each k1), N rows k2, nb transforms}
+        const cuuint64_t n1 = 1ull << log2n1;
+        cuuint64_t dims[3] = {2 * n1, (cuuint64_t)N, (cuuint64_t)nb};
+        cuuint64_t strides[2] = {2 * n1 * sizeof(float), (cuuint64_t)N * 2 * n1 * sizeof(float)};
+        cuuint32_t box[3] = {2 * W, BR, 1};
+        cuuint32_t estr[3] = {1, 1, 1};
+        CUtensorMap map;
+        if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, out, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+            return cudaSuccess;  // not encodable here: the caller runs the plain kernel
+        const size_t smem = FsTmaB<N>::SMEM;
+        auto kern = dir < 0 ? k_fourstep_b_tma<N, -1> : k_fourstep_b_tma<N, 1>;
+        cudaError_t e = set_smem_attrs((const void *)kern, smem, K::MINB);
+        if (e != cudaSuccess) return e;
+        dim3 grid((unsigned)(n1 / W), (unsigned)nb);
+        kern<<<grid, W * K::T, smem, s>>>(static_cast<const float2 *>(tmp), map, log2n1,
+                                          static_cast<const float2 *>(tw), (float)scale, status);
+        *used = true;
+        return cudaGetLastError();
+    }
+}
+
+template <int N, typename R>
 static cudaError_t run_b(const void *tmp, void *out, int log2n1, long long nb, int dir, const void *tw, double scale,
-                         cudaStream_t s) {
+                         int *status, cudaStream_t s) {
+    if (nb > 65535) return cudaErrorInvalidConfiguration;
+    bool used = false;
+    cudaError_t te = run_b_tma<N, R>(tmp, out, log2n1, nb, dir, tw, scale, status, s, &used);
+    if (te != cudaSuccess || used) return te;
     typedef typename cvec<R>::type C;
     typedef FsCfg<N, R> K;
     constexpr int W = K::WMAX;  // <= 64 <= the other factor (>= 2^7)
-    const size_t smem = (size_t)padded_len(N) * W * sizeof(C);
+    const size_t smem = (size_t)K::PL * W * sizeof(C);
     auto kern = dir < 0 ? k_fourstep_b<N, -1, R> : k_fourstep_b<N, 1, R>;
     cudaError_t e = set_smem_attrs((const void *)kern, smem, K::MINB);
     if (e != cudaSuccess) return e;
@@ -281,10 +406,10 @@ static cudaError_t dispatch_a(const void *in, void *tmp, int l1, int l2, long lo
 
 template <typename R>
 static cudaError_t dispatch_b(const void *tmp, void *out, int l1, int l2, long long nb, int dir, const void *tw,
-                              double scale, cudaStream_t s) {
+                              double scale, int *status, cudaStream_t s) {
     switch (l2) {
 #define GBFFT_B(L) \
-    case L: return run_b<(1 << L), R>(tmp, out, l1, nb, dir, tw, scale, s);
+    case L: return run_b<(1 << L), R>(tmp, out, l1, nb, dir, tw, scale, status, s);
         GBFFT_FS_CASES(GBFFT_B)
 #undef GBFFT_B
         default: return cudaErrorInvalidValue;
@@ -302,11 +427,11 @@ cudaError_t launch_fourstep_a(const void *in, void *tmp, int log2n, long long ba
 }
 
 cudaError_t launch_fourstep_b(const void *tmp, void *out, int log2n, long long batch, bool dbl, int dir,
-                              const void *tw_n2, double scale, cudaStream_t s) {
+                              const void *tw_n2, double scale, int *status, cudaStream_t s) {
     int l1, l2;
     fourstep_split(log2n, dbl, &l1, &l2);
-    return dbl ? dispatch_b<double>(tmp, out, l1, l2, batch, dir, tw_n2, scale, s)
-               : dispatch_b<float>(tmp, out, l1, l2, batch, dir, tw_n2, scale, s);
+    return dbl ? dispatch_b<double>(tmp, out, l1, l2, batch, dir, tw_n2, scale, status, s)
+               : dispatch_b<float>(tmp, out, l1, l2, batch, dir, tw_n2, scale, status, s);
 }
 
 }  // namespace gbfft

@@ -52,7 +52,7 @@ cudaError_t launch_fourstep_a(const void *in, void *tmp, int log2n, long long ba
                               const void *tw_n1, const void *tw_4s, const void *tw_coarse, int *status,
                               cudaStream_t s);
 cudaError_t launch_fourstep_b(const void *tmp, void *out, int log2n, long long batch, bool dbl, int dir,
-                              const void *tw_n2, double scale, cudaStream_t s);
+                              const void *tw_n2, double scale, int *status, cudaStream_t s);
 
 // 2D pipeline stages (float32 images).  Intermediate, per image: half spectra
 // [cols/2][rows] complex64, column-major in slot order (layout.cuh; column 0

@@ -168,8 +168,9 @@ def test_cluster_path_against_oracle_and_four_step(gb, log2n, batch):
 
 @pytest.mark.parametrize("log2n,batch", [(18, 3), (20, 2), (22, 1), (24, 1)])
 def test_tma_four_step_and_device_status(gb, log2n, batch):
-    """Complex64 four-step lengths stage pass A's tiles with the TMA; results
-    match the oracle and the plan's device status word stays clear."""
+    """Complex64 four-step lengths move their tiles with the TMA (pass A: tensor
+    loads; pass B: bulk loads and tensor stores); results match the oracle and
+    the plan's device status word stays clear."""
     import torch
 
     n = 1 << log2n
