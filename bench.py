@@ -69,10 +69,10 @@ def measured_peaks():
 # while they are unchanged)
 # (the FP32 kernels include the tensor-core policy header but use none of it)
 STAGE_SOURCES = {
-    "rows_fwd": ("rows.cu", "rows_impl.cuh", "fft_core.cuh", "layout.cuh"),
-    "rows_inv": ("rows.cu", "rows_impl.cuh", "fft_core.cuh", "layout.cuh"),
-    "filter_prep": ("rows.cu", "rows_impl.cuh", "fft_core.cuh", "layout.cuh"),
-    "cols_filter": ("cols.cu", "cols_impl.cuh", "fft_core.cuh", "layout.cuh"),
+    "rows_fwd": ("rows.cu", "rows_impl.cuh", "fft_core.cuh", "layout.cuh", "tma.cuh"),
+    "rows_inv": ("rows.cu", "rows_impl.cuh", "fft_core.cuh", "layout.cuh", "tma.cuh"),
+    "filter_prep": ("rows.cu", "rows_impl.cuh", "fft_core.cuh", "layout.cuh", "tma.cuh"),
+    "cols_filter": ("cols.cu", "cols_impl.cuh", "fft_core.cuh", "layout.cuh", "tma.cuh"),
     "onchip": ("onchip.cu", "fft_core.cuh", "layout.cuh"),
     "fourstep_a": ("fourstep.cu", "fft_core.cuh", "tma.cuh"),
     "fourstep_b": ("fourstep.cu", "fft_core.cuh", "tma.cuh"),

@@ -110,14 +110,15 @@ typedef enum {
      * graph on the first call and replay it while the image-pointer array and
      * the launch shapes stay the same; 0 = plain launches. */
     GBFFT_OPT_USE_GRAPH = 8,
-    /* 1 (default) = use the one-launch cluster paths where they apply;
-     * 0 = the multi-pass paths.  2D plans with both sides 16..256: the whole
-     * pipeline of fft2_filter_ifft2 in one launch, one thread-block cluster
-     * per image holding its half spectra in shared memory (ignored with
-     * GBFFT_OPT_PRECISION != 0).  1D complex64 plans of length 2^15..2^17:
-     * one cluster per transform, the four-step intermediate in distributed
-     * shared memory (one HBM read and one write instead of two each).  Same
-     * results up to rounding order. */
+    /* One-launch cluster paths.  2D plans with both sides 16..256: 1 (default)
+     * or 2 = the whole pipeline of fft2_filter_ifft2 in one launch, one
+     * thread-block cluster per image holding its half spectra in shared
+     * memory (ignored with GBFFT_OPT_PRECISION != 0); 0 = the three-pass
+     * path.  1D complex64 plans of length 2^15..2^17: 2 = one cluster per
+     * transform, the four-step intermediate in distributed shared memory (one
+     * HBM read and one write instead of two each); 0 or 1 (default) = the
+     * four-step passes, which are faster at these lengths.  Same results up
+     * to rounding order. */
     GBFFT_OPT_ONCHIP = 9
 } gbfft_option;
 

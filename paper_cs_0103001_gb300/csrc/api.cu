@@ -242,7 +242,7 @@ int run_1d(gbfft_plan *p, const void *in, void *out, int dir, cudaStream_t s) {
             return launch_fft1d(in, out, p->log2n, p->batch, dbl, dir, p->ws + p->off_tw0, scale, s);
         });
     }
-    if (p->opt_onchip && fft1d_cluster_supported(p->log2n, dbl)) {
+    if (p->opt_onchip == 2 && fft1d_cluster_supported(p->log2n, dbl)) {
         return launch(p, GBFFT_STAGE_FFT1D_CLUSTER, s, [&] {
             return launch_fft1d_cluster(in, out, p->log2n, p->batch, dir, p->ws + p->off_tw0, p->ws + p->off_tw1,
                                         p->ws + p->off_tw3, scale, s);
@@ -403,7 +403,7 @@ int fft_plan_set_option(gbfft_plan_t p, int key, int64_t value) {
             drop_graph(p);
             return GBFFT_OK;
         case GBFFT_OPT_ONCHIP:
-            if (p->kind == KIND_BATCH || (value != 0 && value != 1)) return GBFFT_ERR_INVALID_VALUE;
+            if (p->kind == KIND_BATCH || value < 0 || value > 2) return GBFFT_ERR_INVALID_VALUE;
             p->opt_onchip = value;
             return GBFFT_OK;
         case GBFFT_OPT_ENABLE_BACKWARD:
@@ -550,7 +550,8 @@ static int pipeline_chunk(gbfft_plan *p, const float *img, const float *H, float
     const long long hs_img = per_image ? half_px : 0, beta_img = per_image ? rows : 0;
     rc = launch(p, GBFFT_STAGE_COLS, s, [&] {
         return terms ? launch_cols_tc(spec, hs, beta, hs_img, beta_img, rows, cols, nb, p->ws + p->off_tw1, terms, s)
-                     : launch_cols_filter(spec, hs, beta, hs_img, beta_img, rows, cols, nb, p->ws + p->off_tw1, s);
+                     : launch_cols_filter(spec, hs, beta, hs_img, beta_img, rows, cols, nb, p->ws + p->off_tw1,
+                                                          reinterpret_cast<int *>(p->ws + p->off_status), s);
     });
     if (rc) return rc;
     return launch(p, GBFFT_STAGE_ROWS_INV, s, [&] {

@@ -4,6 +4,7 @@
 
 #include "cols_impl.cuh"
 #include "internal.h"
+#include "tma.cuh"
 
 namespace gbfft {
 
@@ -101,10 +102,190 @@ cudaError_t launch_cols_spectrum(const void *spec, float *mag_T, float *nyq, flo
     }
 }
 
+// ---- The column pass through the TMA (columns of N >= 4096 rows, one per
+// block at a time).  A column's N slots (contiguous, slot order) are viewed
+// as N/16 rows of 128 bytes and move as one 2D tensor box with the 128-byte
+// swizzle (the 16-byte chunk c of row r sits at chunk c ^ (r mod 8)), which
+// keeps the threads' slot-order reads and writes free of bank conflicts; the
+// prepared filter column arrives by a bulk copy.  Each block is persistent:
+// while it transforms one column in one buffer, the next column and its
+// filter are already loading into the other (one mbarrier per buffer,
+// bounded waits as in fourstep.cu).  Results go back into the buffer in the
+// swizzled slot layout and leave by tensor stores; before a buffer is
+// reloaded, its stores must have read it.  The arithmetic is cols_body's.
+template <int N> struct ColTmaCfg {
+    typedef ColCfg<N> C;
+    static constexpr int E = C::E, T = C::T, THREADS = C::THREADS;
+    static_assert(C::W == 1 && T >= 64, "one column per block, slot rows aligned to the swizzle");
+    static constexpr int ROWS = N / 16, BOXR = ROWS < 256 ? ROWS : 256;
+    static constexpr size_t BUF = ((size_t)padded_len(N) * sizeof(float2) + 1023) / 1024 * 1024;
+    static constexpr size_t FB = (size_t)N * sizeof(float);
+    static constexpr size_t SMEM = 1024 + 2 * BUF + 2 * FB + 32;  // alignment slack, buffers, 2 mbarriers
+};
+
+// float2 index of slot s in a column tile stored with the 128-byte swizzle
+__device__ __forceinline__ int swz128(int s) {
+    const int row = s >> 4;
+    return (row << 4) + ((((s >> 1) & 7) ^ (row & 7)) << 1) + (s & 1);
+}
+
+// One column of k_cols_filter_tma in buffer b (its copies complete), from the
+// slot reads to the issue of its tensor stores.  Out of line: compiled on its
+// own, so nothing of one column (twiddles, addresses) is kept in registers
+// across the loop over columns.
+template <int N>
+__device__ __noinline__ void cols_tma_column(const CUtensorMap *map, float2 *bf, const float *h,
+                                             const float *bt, long long c, bool col0, bool prefetch, int b,
+                                             const float2 *__restrict__ tw, int log2g, unsigned char *base,
+                                             const float *hs, long long hs_img, int log2half) {
+    typedef ColTmaCfg<N> K;
+    constexpr int E = K::E, T = K::T;
+    const int t = threadIdx.x;
+    const int G = 1 << log2g;
+    // slots of rows t + T e (layout.cuh), affine in e because G divides T:
+    // side 0 (e < E/2): b0 + 2 T e; side 1: b1 + 2 T (E - 1 - e), except row
+    // N/2 (t = 0, e = E/2) in slot G.  2 T is a whole number of 8-row swizzle
+    // blocks, so the swizzled index is affine in e as well.
+    const int b0 = ((t >> log2g) << (log2g + 1)) + (t & (G - 1));
+    const int b1 = (((-t) >> log2g) << (log2g + 1)) + G + ((-t) & (G - 1)) + 2 * T;
+    const int i0 = swz128(b0), i1 = swz128(b1), ig = swz128(G);
+    auto sidx = [&](int e) { return e < E / 2 ? i0 + 2 * T * e : (e == E / 2 && t == 0 ? ig : i1 + 2 * T * (E - 1 - e)); };
+    float2 v[E];
+#pragma unroll
+    for (int e = 0; e < E; ++e) v[e] = bf[sidx(e)];
+    if (prefetch && t == 0) {  // the next column and its filter into the other buffer
+        const long long cn = c + gridDim.x;
+        float2 *nb = reinterpret_cast<float2 *>(base + (b ^ 1) * K::BUF);
+        float *nf = reinterpret_cast<float *>(base + 2 * K::BUF + (b ^ 1) * K::FB);
+        uint64_t *bar = reinterpret_cast<uint64_t *>(base + 2 * K::BUF + 2 * K::FB) + (b ^ 1);
+        bulk_wait_read();  // the other buffer's stores have read it
+        mbar_expect_tx(bar, (uint32_t)(N * sizeof(float2) + N * sizeof(float)));
+        for (int r = 0; r < K::ROWS; r += K::BOXR) tma_load_2d(nb + r * 16, map, 0, (int)(cn * K::ROWS + r), bar);
+        bulk_load(nf, hs + (cn >> log2half) * hs_img + (cn & ((1LL << log2half) - 1)) * N, N * sizeof(float), bar);
+    }
+    // the first exchange starts with a block barrier: every thread has read
+    // its slots before the buffer becomes the exchange buffer
+    fft_regs<N, E, -1>(v, bf, tw, t);
+    if (col0) {  // column 0 needs Q[-u] (uniform per block)
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < E; ++e) bf[pad16(t + T * e)] = v[e];
+        __syncthreads();
+#pragma unroll
+        for (int e = 0; e < E; ++e) {
+            const int u = t + T * e;
+            const float2 qm = bf[pad16((N - u) & (N - 1))];
+            const float hu = h[u], bu = bt[u];
+            v[e] = make_float2(hu * v[e].x + bu * qm.x, hu * v[e].y - bu * qm.y);
+        }
+    } else {
+#pragma unroll
+        for (int e = 0; e < E; ++e) v[e] = cscale(v[e], h[t + T * e]);
+    }
+    fft_regs<N, E, 1>(v, bf, tw, t);
+    __syncthreads();  // the last exchange's reads are complete
+#pragma unroll
+    for (int e = 0; e < E; ++e) bf[sidx(e)] = v[e];
+    fence_async_smem();
+    __syncthreads();
+    if (t == 0) {
+        for (int r = 0; r < K::ROWS; r += K::BOXR) tma_store_2d(map, 0, (int)(c * K::ROWS + r), bf + r * 16);
+        bulk_commit();
+    }
+}
+
+template <int N>
+__global__ void __launch_bounds__(ColCfg<N>::THREADS, 2)
+    k_cols_filter_tma(const __grid_constant__ CUtensorMap map, const float *__restrict__ hs,
+                      const float *__restrict__ beta, long long hs_img, long long beta_img, int log2half,
+                      long long ncols, int log2g, const float2 *__restrict__ tw, int *status) {
+    typedef ColTmaCfg<N> K;
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    unsigned char *base = smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u);  // the swizzle repeats every 1 KB
+    uint64_t *bar = reinterpret_cast<uint64_t *>(base + 2 * K::BUF + 2 * K::FB);
+    const long long hmask = (1LL << log2half) - 1;
+    const int t = threadIdx.x;
+    if (t == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+    }
+    __syncthreads();
+    long long c = blockIdx.x;
+    if (t == 0 && c < ncols) {  // the first column and its filter into buffer 0
+        mbar_expect_tx(&bar[0], (uint32_t)(N * sizeof(float2) + N * sizeof(float)));
+        float2 *b0 = reinterpret_cast<float2 *>(base);
+        for (int r = 0; r < K::ROWS; r += K::BOXR) tma_load_2d(b0 + r * 16, &map, 0, (int)(c * K::ROWS + r), &bar[0]);
+        bulk_load(base + 2 * K::BUF, hs + (c >> log2half) * hs_img + (c & hmask) * N, N * sizeof(float), &bar[0]);
+    }
+    for (int it = 0; c < ncols; c += gridDim.x, ++it) {
+        const int b = it & 1;
+        const bool ok = mbar_wait_bounded(&bar[b], (it >> 1) & 1, kTmaPolls);
+        if (__syncthreads_or(!ok)) {  // uniform: give up on the rest of this block's columns
+            if (t == 0) {
+                atomicExch(status, 1);
+                mbar_wait_bounded(&bar[b], (it >> 1) & 1, kTmaPolls);  // the copies in flight, bounded
+            }
+            break;
+        }
+        cols_tma_column<N>(&map, reinterpret_cast<float2 *>(base + b * K::BUF),
+                           reinterpret_cast<const float *>(base + 2 * K::BUF + b * K::FB),
+                           beta + (c >> log2half) * beta_img, c, (c & hmask) == 0, c + gridDim.x < ncols, b, tw,
+                           log2g, base, hs, hs_img, log2half);
+    }
+    if (t == 0) bulk_wait_read();  // every store has read its buffer before the block's memory goes
+}
+
+template <int N>
+static cudaError_t run_cols_tma(void *spec, const float *hs, const float *beta, long long hs_img, long long beta_img,
+                                int cols, int nimg, int log2g, const void *tw, int *status, cudaStream_t s,
+                                bool *used) {
+    typedef ColTmaCfg<N> K;
+    *used = false;
+    const EncodeTiledFn enc = encode_tiled();
+    if (!enc || !status || hs_img % 4 != 0) return cudaSuccess;
+    const long long ncols = (long long)(cols / 2) * nimg;
+    if (ncols * K::ROWS > 0x7fffffffLL) return cudaSuccess;
+    // the spectra as rows of 16 slots (128 bytes): {32 floats, ncols * N / 16 rows}
+    cuuint64_t dims[2] = {32, (cuuint64_t)(ncols * K::ROWS)};
+    cuuint64_t strides[1] = {128};
+    cuuint32_t box[2] = {32, (cuuint32_t)K::BOXR};
+    cuuint32_t estr[2] = {1, 1};
+    CUtensorMap map;
+    if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, spec, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+            CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaSuccess;
+    auto kern = k_cols_filter_tma<N>;
+    static int slots = 0;  // resident blocks (per process; one device type)
+    if (slots == 0) {
+        cudaError_t e = set_smem_attrs((const void *)kern, K::SMEM, 2);
+        int dev = 0, sms = 0, per_sm = 0;
+        if (e == cudaSuccess) e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, K::THREADS, K::SMEM);
+        if (e != cudaSuccess) return e;
+        if (per_sm < 1) return cudaSuccess;
+        slots = sms * per_sm;
+    }
+    const long long rounds = (ncols + slots - 1) / slots;
+    const long long grid = (ncols + rounds - 1) / rounds;  // the fewest blocks for the same number of rounds
+    kern<<<(unsigned)grid, K::THREADS, K::SMEM, s>>>(map, hs, beta, hs_img, beta_img, ilog2(cols / 2), ncols, log2g,
+                                                     static_cast<const float2 *>(tw), status);
+    *used = true;
+    return cudaGetLastError();
+}
+
 template <int N>
 static cudaError_t run_cols(void *spec, const float *hs, const float *beta, long long hs_img, long long beta_img,
-                            int cols, int nimg, int log2g, const void *tw, cudaStream_t s) {
+                            int cols, int nimg, int log2g, const void *tw, int *status, cudaStream_t s) {
     typedef ColCfg<N> K;
+    if constexpr (N >= 4096 && K::W == 1 && K::THREADS == 256) {
+        if ((1 << log2g) <= K::T && cols >= 4) {
+            bool used = false;
+            cudaError_t e = run_cols_tma<N>(spec, hs, beta, hs_img, beta_img, cols, nimg, log2g, tw, status, s, &used);
+            if (e != cudaSuccess || used) return e;
+        }
+    }
     auto kern = k_cols_filter<N>;
     cudaError_t e = set_smem_attrs((const void *)kern, K::SMEM, 2);
     if (e != cudaSuccess) return e;
@@ -162,13 +343,13 @@ cudaError_t launch_cols_analytic(void *spec, int kind, double p0, double p1, int
 }
 
 cudaError_t launch_cols_filter(void *spec, const float *hs, const float *beta, long long hs_img, long long beta_img,
-                               int rows, int cols, int nimg, const void *tw_rows, cudaStream_t s) {
+                               int rows, int cols, int nimg, const void *tw_rows, int *status, cudaStream_t s) {
     int g = rows_pairs_per_block(cols);
     if (g > rows / 2) g = rows / 2;
     const int log2g = ilog2(g);
     switch (ilog2(rows)) {
 #define GBFFT_CASE(L) \
-    case L: return run_cols<(1 << L)>(spec, hs, beta, hs_img, beta_img, cols, nimg, log2g, tw_rows, s);
+    case L: return run_cols<(1 << L)>(spec, hs, beta, hs_img, beta_img, cols, nimg, log2g, tw_rows, status, s);
         GBFFT_CASE(1) GBFFT_CASE(2) GBFFT_CASE(3) GBFFT_CASE(4) GBFFT_CASE(5) GBFFT_CASE(6) GBFFT_CASE(7)
         GBFFT_CASE(8) GBFFT_CASE(9) GBFFT_CASE(10) GBFFT_CASE(11) GBFFT_CASE(12) GBFFT_CASE(13)
 #undef GBFFT_CASE

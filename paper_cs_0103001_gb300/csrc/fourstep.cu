@@ -250,26 +250,6 @@ __global__ void __launch_bounds__(FsCfg<N, float>::MAXT, FsCfg<N, float>::MINB)
     }
 }
 
-typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
-                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-// cuTensorMapEncodeTiled from the driver (looked up once; null if unavailable)
-static EncodeTiledFn encode_tiled() {
-    static const EncodeTiledFn fn = [] {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
-                cudaSuccess ||
-            q != cudaDriverEntryPointSuccess) {
-            cudaGetLastError();
-            return (EncodeTiledFn) nullptr;
-        }
-        return reinterpret_cast<EncodeTiledFn>(p);
-    }();
-    return fn;
-}
-
 template <int N, typename R>
 static cudaError_t run_a_tma(const void *in, void *tmp, int log2n2, long long nb, int dir, const void *tw,
                              const void *t4, int log2f, const void *t5, int *status, cudaStream_t s, bool *used) {

@@ -84,7 +84,7 @@ cudaError_t launch_cols_analytic(void *spec, int kind, double p0, double p1, int
                                  const void *tw_rows, cudaStream_t s);
 // hs_img / beta_img: elements between images' prepared filters (0 = shared)
 cudaError_t launch_cols_filter(void *spec, const float *hs, const float *beta, long long hs_img, long long beta_img,
-                               int rows, int cols, int nimg, const void *tw_rows, cudaStream_t s);
+                               int rows, int cols, int nimg, const void *tw_rows, int *status, cudaStream_t s);
 cudaError_t launch_rows_inv(const void *spec, float *out, int rows, int cols, int nimg, const void *tw_cols,
                             cudaStream_t s);
 // Tensor-core variants (tc2d.cu): radix-16 passes as split-BF16 DFT-matrix

@@ -109,9 +109,51 @@ static int log2_pairs_per_block(int rows, int cols) {
     return ilog2(g);
 }
 
+// The forward row pass with its half-spectrum runs leaving by tensor stores
+// (rows_fwd_body with TSTORE): every block holds G = PPC pairs.
+template <int M>
+__global__ void __launch_bounds__(RowCfg<M>::THREADS, RowCfg<M>::THREADS <= 512 ? 2 : 1)
+    k_rows_fwd_tma(const float *__restrict__ img, float2 *__restrict__ spec, int N, int log2g,
+                   const float2 *__restrict__ tw, const __grid_constant__ CUtensorMap omap) {
+    extern __shared__ __align__(128) unsigned char smraw[];
+    unsigned char *base = smraw + ((128u - (smem_u32(smraw) & 127u)) & 127u);  // TMA wants 128-byte alignment
+    const size_t y = blockIdx.y;
+    rows_fwd_body<M, Fp32Fft, false, true>(img + y * N * M, spec + y * (M / 2) * N, N, log2g, tw, blockIdx.x, base,
+                                           Fp32Fft(), Crop{0, 0}, &omap, (int)y);
+}
+
+// Tensor map of the half spectra of nimg images ({2 rows floats, cols/2
+// columns, images}, box {4 G floats, up to 256 columns, 1}) for
+// k_rows_fwd_tma; false if the driver offers no encoder or refuses.
+static bool spec_map(CUtensorMap *map, void *spec, int rows, int cols, int nimg, int g) {
+    const EncodeTiledFn enc = encode_tiled();
+    if (!enc) return false;
+    const cuuint64_t h2 = (cuuint64_t)cols / 2;
+    cuuint64_t dims[3] = {2 * (cuuint64_t)rows, h2, (cuuint64_t)nimg};
+    cuuint64_t strides[2] = {(cuuint64_t)rows * 8, h2 * rows * 8};
+    cuuint32_t box[3] = {(cuuint32_t)(4 * g), (cuuint32_t)(h2 < 256 ? h2 : 256), 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, spec, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int M>
 static cudaError_t run_rows_fwd(const float *img, void *spec, int rows, int nimg, const void *tw, cudaStream_t s) {
     typedef RowCfg<M> K;
+    if constexpr (M >= 256 && 4 * K::PPC <= 256 && K::THREADS <= 512) {
+        const int lg = log2_pairs_per_block(rows, M);
+        CUtensorMap map;
+        if ((1 << lg) == K::PPC && spec_map(&map, spec, rows, M, nimg, K::PPC)) {
+            const size_t smem = K::SMEM_FWD + 128;
+            cudaError_t e = set_smem<M>((const void *)k_rows_fwd_tma<M>, smem);
+            if (e != cudaSuccess) return e;
+            dim3 grid((rows / 2) >> lg, nimg);
+            k_rows_fwd_tma<M><<<grid, K::THREADS, smem, s>>>(img, static_cast<float2 *>(spec), rows, lg,
+                                                             static_cast<const float2 *>(tw), map);
+            return cudaGetLastError();
+        }
+    }
     cudaError_t e = set_smem<M>((const void *)k_rows_fwd<M>, K::SMEM_FWD);
     if (e != cudaSuccess) return e;
     const int lg = log2_pairs_per_block(rows, M);

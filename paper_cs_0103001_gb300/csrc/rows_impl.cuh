@@ -18,6 +18,7 @@
 #include "fft_core.cuh"
 #include "fft_tc.cuh"
 #include "layout.cuh"
+#include "tma.cuh"
 
 namespace gbfft {
 
@@ -64,11 +65,16 @@ __device__ __forceinline__ float2 split_ab(const float2 *exg, int k, bool side) 
 // block-wide barrier-free epilogue, so a caller that reuses shared memory
 // must synchronise first.
 // With PAD, img is the crop.rows x crop.cols sub-image (pitch crop.cols) and
-// the rest of the grid reads as zero.
-template <int M, typename FFT = Fp32Fft, bool PAD = false>
+// the rest of the grid reads as zero.  With TSTORE (G >= 2) the block's run
+// of 2G slots of every column is gathered in shared memory as the dense box
+// [k][2G] and leaves by tensor stores through omap (a 3D view {2N floats,
+// M/2 columns, images} of the half spectra) at image z; smraw is then
+// 128-byte aligned.
+template <int M, typename FFT = Fp32Fft, bool PAD = false, bool TSTORE = false>
 __device__ __forceinline__ void rows_fwd_body(const float *__restrict__ img, float2 *__restrict__ spec, int N,
                                               int log2g, const float2 *__restrict__ tw, int bx,
-                                              unsigned char *smraw, FFT fft = FFT(), Crop crop = Crop{0, 0}) {
+                                              unsigned char *smraw, FFT fft = FFT(), Crop crop = Crop{0, 0},
+                                              const CUtensorMap *omap = nullptr, int z = 0) {
     typedef RowCfg<M> K;
     constexpr int E = K::E, T = K::T, H2 = M / 2;
     float2 *sm = reinterpret_cast<float2 *>(smraw);
@@ -109,7 +115,38 @@ __device__ __forceinline__ void rows_fwd_body(const float *__restrict__ img, flo
     // consecutive slots s, s + 1 of the block's run of 2G (s < G: A of pairs
     // s, s + 1; s >= G: B of pairs s - G, s - G + 1), 16 bytes per store
     float2 *sb = spec + (size_t)bx * 2 * G;
-    if (G >= 2) {
+    if constexpr (TSTORE) {
+        // every unit (k, s) of the block, K::UNITS per thread, into registers;
+        // then into the box [k][2G] over the exchange buffers (16-byte stores,
+        // consecutive units adjacent) and out by the TMA
+        // G = PPC here (the launcher checks): H2 G units over G T threads, 8 each
+        constexpr int U = (H2 * K::PPC) / K::THREADS;
+        static_assert(U == 8 && 4 * K::PPC <= 256, "8 units per thread; box of at most 256 floats wide");
+        float4 out[U];
+#pragma unroll
+        for (int i = 0; i < U; ++i) {
+            const int idx = threadIdx.x + i * K::THREADS;
+            const int k = idx >> log2g, s = (idx & (G - 1)) * 2;
+            const bool side = s >= G;
+            const int g0 = side ? s - G : s;
+            const float2 x0 = split_ab<M>(sm + g0 * padded_len(M), k, side);
+            const float2 x1 = split_ab<M>(sm + (g0 + 1) * padded_len(M), k, side);
+            out[i] = make_float4(x0.x, x0.y, x1.x, x1.y);
+        }
+        __syncthreads();  // every read of the exchange buffers is complete
+        float4 *box = reinterpret_cast<float4 *>(sm);
+#pragma unroll
+        for (int i = 0; i < U; ++i) box[threadIdx.x + i * K::THREADS] = out[i];
+        fence_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            constexpr int BK = H2 < 256 ? H2 : 256;  // columns per box
+            for (int k0 = 0; k0 < H2; k0 += BK)
+                tma_store_3d(omap, bx * 4 * G, k0, z, sm + (size_t)k0 * 2 * G);
+            bulk_commit();
+            bulk_wait_read();
+        }
+    } else if (G >= 2) {
         const int n = H2 << log2g;
         for (int idx = threadIdx.x; idx < n; idx += K::THREADS) {
             const int k = idx >> log2g, s = (idx & (G - 1)) * 2;
