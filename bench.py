@@ -431,9 +431,10 @@ def _timed(fn, steps, warm, flush=None):
     return statistics.median(ms)
 
 
-def variant_fft1d(log2n: int, dtype: str = "c64", steps: int = 10):
+def variant_fft1d(log2n: int, dtype: str = "c64", steps: int = 10, onchip: int = 1):
     """Batched 1D transforms (Eq. E2 forward), batch x N = 2^26 complex64
-    (complex128: N = 2^20, batch 64); GB/s of one read + one write."""
+    (complex128: N = 2^20, batch 64); GB/s of one read + one write.  onchip:
+    the plan's GBFFT_OPT_ONCHIP (2 = the cluster path at 2^15..2^17)."""
     import torch
 
     import paper_cs_0103001_gb300 as gb
@@ -446,7 +447,9 @@ def variant_fft1d(log2n: int, dtype: str = "c64", steps: int = 10):
         batch, tdt = 64, torch.complex128
     x = torch.from_numpy(synth.complex_uniform((batch, n), 2, log2n)).cuda().to(tdt)
     y = torch.empty_like(x)
-    plan = gb.Plan1D(n, batch, tdt, "cuda")
+    from paper_cs_0103001_gb300 import _native as nat
+
+    plan = gb.Plan1D(n, batch, tdt, "cuda", {nat.OPT_ONCHIP: onchip})
     ms = _timed(lambda: plan.forward(x, out=y), steps, 3)
     nbytes = 2 * x.numel() * x.element_size()
     return {"n": n, "batch": batch, "dtype": dtype, "us": round(ms * 1e3, 1),
@@ -640,7 +643,7 @@ def run_workload(args):
 
     torch.cuda.set_device(0)
     if args.workload == "fft1d":
-        res = variant_fft1d(args.log2n, args.dtype, args.steps)
+        res = variant_fft1d(args.log2n, args.dtype, args.steps, args.onchip)
     elif args.workload == "batched":
         res = variant_batched(steps=args.steps)
     elif args.workload == "pipeline256":
@@ -689,6 +692,8 @@ def main():
                     choices=["pipeline4096", "fft1d", "batched", "pipeline256", "backward2048"])
     ap.add_argument("--log2n", type=int, default=20)
     ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
+    ap.add_argument("--onchip", type=int, default=1, choices=[0, 1, 2],
+                    help="--workload fft1d: the plan's on-chip option (2 = cluster path at 2^15..2^17)")
     ap.add_argument("--no-variants", dest="variants", action="store_false",
                     help="headline only, without the other workloads")
     args = ap.parse_args()
