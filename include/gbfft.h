@@ -302,10 +302,18 @@ int gbfft_plan_profile_read(gbfft_plan_t plan, double *ms, int64_t *launches, in
 
 /* Read and clear the plan's device status word (synchronous: waits for the
  * plan's work on the device).  Kernels that wait on asynchronous copies (the
- * TMA-staged four-step pass of 1D complex64 plans) wait a bounded time; one
- * that gives up leaves its outputs unwritten and records it here:
- * GBFFT_ERR_TIMEOUT.  GBFFT_OK otherwise. */
+ * TMA-fed four-step passes of 1D complex64 plans and column pass of 2D plans)
+ * wait a bounded time; one that gives up leaves its outputs unwritten and
+ * records it here: GBFFT_ERR_TIMEOUT.  GBFFT_OK otherwise. */
 int gbfft_device_status(gbfft_plan_t plan);
+
+/* Diagnostic of that path: launches on `stream` one block that waits on an
+ * mbarrier no copy will ever complete, testing it at most `polls` times
+ * (1 .. 2^22, each test followed by a 64 ns sleep); the wait gives up, records
+ * a timeout in the plan's device status word, and the block returns.  The
+ * next gbfft_device_status returns GBFFT_ERR_TIMEOUT.  Needs a bound
+ * workspace; GBFFT_ERR_INVALID_VALUE for polls out of range. */
+int gbfft_selftest_wait_timeout(gbfft_plan_t plan, int64_t polls, gbfft_stream_t stream);
 
 /* Library version as 10000*major + 100*minor + patch. */
 int gbfft_version(void);

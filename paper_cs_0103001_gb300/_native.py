@@ -66,6 +66,7 @@ SIGNATURES = {
     "fft2_spectrum": (_INT, [_P, _P, _I64, _I64, _P, _P]),
     "fft2_filter_ifft2_analytic": (_INT, [_P, _P, _INT, ctypes.c_double, ctypes.c_double, _P, _P]),
     "gbfft_device_status": (_INT, [_P]),
+    "gbfft_selftest_wait_timeout": (_INT, [_P, _I64, _P]),
     "fft2_filter_ifft2_backward": (_INT, [_P, _P, _P, _P, _P, _P, _P]),
     "fft_plan_destroy": (_INT, [_P]),
     "fft2_batched_plan_create": (_INT, [_INT, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_P)]),

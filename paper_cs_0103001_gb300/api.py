@@ -64,6 +64,11 @@ class _PlanBase:
         """Raise if a kernel of this plan gave up a bounded wait (synchronous)."""
         nat.call("gbfft_device_status", self.handle)
 
+    def selftest_wait_timeout(self, polls: int = 1 << 16) -> None:
+        """Launch the diagnostic block whose bounded wait runs out (sets this
+        plan's device status word; see gbfft_selftest_wait_timeout)."""
+        nat.call("gbfft_selftest_wait_timeout", self.handle, polls, _stream_handle(self.device))
+
     def profile_read(self) -> dict[str, tuple[float, int]]:
         n = len(nat.STAGES)
         ms = (ctypes.c_double * n)()

@@ -11,6 +11,7 @@
 #include "batched.h"
 #include "gbfft.h"
 #include "internal.h"
+#include "tma.cuh"
 
 using namespace gbfft;
 
@@ -930,6 +931,15 @@ int gbfft_device_status(gbfft_plan_t p) {
     if (e == cudaSuccess && word != 0) e = cudaMemset(p->ws + p->off_status, 0, sizeof(int));
     if (e != cudaSuccess) return cuda_fail(e);
     return word ? GBFFT_ERR_TIMEOUT : GBFFT_OK;
+}
+
+int gbfft_selftest_wait_timeout(gbfft_plan_t p, int64_t polls, gbfft_stream_t stream) {
+    int rc = check_plan_ready(p);
+    if (rc) return rc;
+    if (polls < 1 || polls > (int64_t)kTmaPolls) return GBFFT_ERR_INVALID_VALUE;
+    cudaError_t e = launch_wait_timeout(reinterpret_cast<int *>(p->ws + p->off_status), (unsigned)polls,
+                                        static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? GBFFT_OK : cuda_fail(e);
 }
 
 int fft_plan_destroy(gbfft_plan_t p) {

@@ -35,6 +35,9 @@ cudaError_t launch_fft1d_cluster(const void *in, void *out, int log2n, long long
                                  const void *tw_n2, const void *tw_full, double scale, cudaStream_t s);
 // complex64 table [n1][n2] of W_n^(k1 j2), each rounded once from FP64
 cudaError_t launch_fourstep_full_twiddles(void *tw, int n, int log2n2, cudaStream_t s);
+// One block whose bounded mbarrier wait cannot succeed: sets *status after
+// `polls` tests (selftest.cu).
+cudaError_t launch_wait_timeout(int *status, unsigned polls, cudaStream_t s);
 // Coarse inter-pass table of the split n = n1 n2 (n1 >= 16): entry e * n2 + j2
 // holds W_(16 n2)^(e j2) = W_n^((n1/16) e j2), e < 16, j2 < n2.
 cudaError_t launch_fourstep_coarse_twiddles(void *tw, int n2, bool dbl, cudaStream_t s);

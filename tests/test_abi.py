@@ -135,4 +135,6 @@ def test_device_status_checks(nat):
     rc, h = _plan(nat, n=1 << 20, batch=1)
     assert rc == nat.OK
     assert nat.lib.gbfft_device_status(h) == nat.ERR_WORKSPACE  # nothing bound yet
+    assert nat.lib.gbfft_selftest_wait_timeout(None, 1, None) == nat.ERR_NULL
+    assert nat.lib.gbfft_selftest_wait_timeout(h, 16, None) == nat.ERR_WORKSPACE
     assert nat.lib.fft_plan_destroy(h) == nat.OK

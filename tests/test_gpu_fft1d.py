@@ -184,3 +184,29 @@ def test_tma_four_step_and_device_status(gb, log2n, batch):
     plan.device_status()  # raises on a timed-out wait
     assert max_rel_l2(f, oracle.fft(xo), axes=-1) <= tol_fp32(n)
     assert max_rel_l2(b, oracle.ifft(xo), axes=-1) <= tol_fp32(n)
+
+
+def test_bounded_wait_timeout_is_reported_and_the_plan_stays_usable(gb):
+    """The diagnostic block arms an mbarrier that no copy completes: its
+    bounded wait runs out, the status word records it, device_status raises
+    GBFFT_ERR_TIMEOUT once (and clears it), and the plan's next transform is
+    still correct: the context was not lost."""
+    import torch
+
+    from paper_cs_0103001_gb300 import _native as nat
+
+    n, batch = 1 << 20, 1
+    plan = gb.Plan1D(n, batch, torch.complex64, "cuda")
+    plan.device_status()  # clear
+    plan.selftest_wait_timeout(1 << 12)
+    with pytest.raises(nat.GbfftError) as err:
+        plan.device_status()
+    assert err.value.status == nat.ERR_TIMEOUT
+    plan.device_status()  # cleared by the read
+    x = synth.complex_uniform((batch, n), 6, 20)
+    f = plan.forward(torch.from_numpy(x).cuda()).cpu().numpy()
+    plan.device_status()
+    assert max_rel_l2(f, oracle.fft(x.astype(np.complex128)), axes=-1) <= tol_fp32(n)
+    with pytest.raises(nat.GbfftError) as err:
+        plan.selftest_wait_timeout(0)  # out of range
+    assert err.value.status == nat.ERR_INVALID_VALUE
