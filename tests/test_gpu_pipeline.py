@@ -80,6 +80,25 @@ def test_batch_per_image_filter_and_chunks(gb):
     assert max_rel_l2(out.reshape(B, rows, cols), oracle.pipeline(img, H[2]), axes=(1, 2)) <= tol_fp32(rows * cols)
 
 
+@pytest.mark.parametrize("cols,chunk", [(64, 3), (16, 0), (512, 2)])
+def test_tall_batches_through_the_persistent_column_pass(gb, cols, chunk):
+    """Images of 4096 rows take the persistent TMA-fed column pass: batches of
+    several images per launch (columns of consecutive images in one walk),
+    per-image filters, and row-pass groups from 2 to 256 pairs."""
+    import torch
+
+    from paper_cs_0103001_gb300 import _native as nat
+
+    rows, B = 4096, 3
+    img = np.stack([synth.sky(rows, cols, 60, 16, b) for b in range(B)])
+    H = np.stack([synth.random_filter(rows, cols, 17, b) for b in range(B)])
+    plan = gb.Plan2D(rows, cols, B, "cuda", {nat.OPT_H_BATCH_STRIDE: rows * cols, nat.OPT_IMAGES_PER_CHUNK: chunk,
+                                            nat.OPT_PROFILE: 1})
+    got = plan.filter(torch.from_numpy(img).cuda(), torch.from_numpy(H).cuda()).cpu().numpy()
+    plan.device_status()
+    assert max_rel_l2(got, oracle.pipeline(img, H), axes=(1, 2)) <= tol_fp32(rows * cols)
+
+
 def test_repeatable_bits(gb):
     import torch
 
