@@ -167,7 +167,7 @@ __device__ __forceinline__ void rows_fwd_body(const float *__restrict__ img, flo
 // One block's share of the inverse row pass: spec [M/2][N] (slot order) of one
 // image -> rows of pairs bx*G .. bx*G + G - 1 of out [N][M], unscaled.
 // With PAD, only the crop.rows x crop.cols sub-image is written (pitch crop.cols).
-template <int M, typename FFT = Fp32Fft, bool PAD = false>
+template <int M, typename FFT = Fp32FftTw15, bool PAD = false>
 __device__ __forceinline__ void rows_inv_body(const float2 *__restrict__ spec, float *__restrict__ out, int N,
                                               int log2g, const float2 *__restrict__ tw, int bx,
                                               unsigned char *smraw, FFT fft = FFT(), Crop crop = Crop{0, 0}) {
