@@ -24,10 +24,10 @@
 // threads read consecutive entries; the sizes telescope to N - 1 entries in
 // all.  Entries hold the forward (negative-exponent) factor; inverse passes
 // use the conjugate.  The table is built once per plan in FP64 and rounded
-// once to the working precision.  A complex64 radix-16 pass may read only
-// the factors r = 1, 2, 3, 4, 8, 12 and form the others as products
-// W^(a + 4b) = W^a W^(4b) (TW6): six loads instead of fifteen, one more
-// rounding for nine of the factors.
+// once to the working precision.  A complex64 radix-16 pass reads only the
+// factors r = 1, 2, 3, 4, 8, 12 and forms the others as products
+// W^(a + 4b) = W^a W^(4b): six loads instead of fifteen, one more rounding
+// for nine of the factors.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -241,7 +241,7 @@ __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wai
 // ------------------------------------------------------- one pass ---------
 // sm: this transform's exchange buffer, element x at sm[pad16(x) * S]
 // (S > 1 interleaves S transforms element by element).
-template <int N, int E, int R, int NS, int DIR, bool LAST, int PS, bool TW6, typename C>
+template <int N, int E, int R, int NS, int DIR, bool LAST, int PS, typename C>
 __device__ __forceinline__ void stockham_pass(C (&v)[E], C *sm, const C *__restrict__ tw, int t, int S) {
     constexpr int T = N / E;
     constexpr int Q = E / R;
@@ -254,7 +254,7 @@ __device__ __forceinline__ void stockham_pass(C (&v)[E], C *sm, const C *__restr
         for (int r = 0; r < R; ++r) a[r] = v[q + r * Q];
         if constexpr (NS > 1) {
             const C *twp = tw + (NS - 1) + (j & (NS - 1));
-            if constexpr (TW6 && R == 16 && sizeof(C) == 8) {
+            if constexpr (R == 16 && sizeof(C) == 8) {
                 C w1[4], w4[4];  // W^q and W^(4q), q = 1..3
 #pragma unroll
                 for (int q = 1; q < 4; ++q) {
@@ -294,13 +294,13 @@ __device__ __forceinline__ void stockham_pass(C (&v)[E], C *sm, const C *__restr
     }
 }
 
-template <int N, int E, int DIR, int P, int PS, bool TW6, typename C> struct Passes {
+template <int N, int E, int DIR, int P, int PS, typename C> struct Passes {
     __device__ __forceinline__ static void run(C (&v)[E], C *sm, const C *__restrict__ tw, int t, int S) {
         constexpr int NP = RadixPlan<N>::P;
         constexpr int R = RadixPlan<N>::radix(P);
         constexpr int NS = RadixPlan<N>::stride(P);
-        stockham_pass<N, E, R, NS, DIR, P == NP - 1, PS, TW6>(v, sm, tw, t, S);
-        if constexpr (P + 1 < NP) Passes<N, E, DIR, P + 1, PS, TW6, C>::run(v, sm, tw, t, S);
+        stockham_pass<N, E, R, NS, DIR, P == NP - 1, PS>(v, sm, tw, t, S);
+        if constexpr (P + 1 < NP) Passes<N, E, DIR, P + 1, PS, C>::run(v, sm, tw, t, S);
     }
 };
 
@@ -308,12 +308,11 @@ template <int N, int E, int DIR, int P, int PS, bool TW6, typename C> struct Pas
 // T = N/E threads of one transform.  On entry and on exit v[e] is element /
 // bin t + T*e.  All threads of the block must call it (it contains
 // __syncthreads when N needs more than one pass).  Element x of the exchange
-// buffer is sm[pad_ps<PS>(x) * S]; S > 1 interleaves S transforms.  TW6:
-// six twiddle loads per complex64 radix-16 butterfly (see the top of the file).
-template <int N, int E, int DIR, int PS = 4, bool TW6 = true, typename C>
+// buffer is sm[pad_ps<PS>(x) * S]; S > 1 interleaves S transforms.
+template <int N, int E, int DIR, int PS = 4, typename C>
 __device__ __forceinline__ void fft_regs(C (&v)[E], C *sm, const C *__restrict__ tw, int t, int S = 1) {
     static_assert(N % E == 0 && E >= RadixPlan<N>::MAXR, "bad elements per thread");
-    Passes<N, E, DIR, 0, PS, TW6, C>::run(v, sm, tw, t, S);
+    Passes<N, E, DIR, 0, PS, C>::run(v, sm, tw, t, S);
 }
 
 }  // namespace gbfft

@@ -197,7 +197,7 @@ template <int N, int DIR, int TERMS, int P> struct PassesTC {
         if constexpr (R == 16) {
             tc_pass16<N, NS, DIR, TERMS>(v, sm, tw, t, S, st);
         } else {
-            stockham_pass<N, 16, R, NS, DIR, P == NP - 1, 4, true>(v, sm, tw, t, S);
+            stockham_pass<N, 16, R, NS, DIR, P == NP - 1, 4>(v, sm, tw, t, S);
         }
         if constexpr (P + 1 < NP) PassesTC<N, DIR, TERMS, P + 1>::run(v, sm, tw, t, S, st);
     }
@@ -218,17 +218,6 @@ struct Fp32Fft {
     __device__ __forceinline__ void run(float2 (&v)[E], float2 *sm, const float2 *__restrict__ tw, int t,
                                         int S = 1) {
         fft_regs<N, E, DIR>(v, sm, tw, t, S);
-    }
-};
-
-// The same with all fifteen twiddles of a radix-16 butterfly read from the
-// table (the inverse row pass measured faster this way: 45.7 against 47.2 us
-// at 4096^2, while the other passes gain from the six-load form).
-struct Fp32FftTw15 {
-    template <int N, int E, int DIR>
-    __device__ __forceinline__ void run(float2 (&v)[E], float2 *sm, const float2 *__restrict__ tw, int t,
-                                        int S = 1) {
-        fft_regs<N, E, DIR, 4, false>(v, sm, tw, t, S);
     }
 };
 

@@ -55,8 +55,8 @@ __global__ void __launch_bounds__(RowCfg<M>::THREADS, RowCfg<M>::THREADS <= 512 
                    long long out_stride, const float2 *__restrict__ tw) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const size_t y = blockIdx.y;
-    rows_inv_body<M, Fp32FftTw15, true>(spec + y * (M / 2) * N, out + y * out_stride, N, log2g, tw, blockIdx.x,
-                                        smraw, Fp32FftTw15(), crop);
+    rows_inv_body<M, Fp32Fft, true>(spec + y * (M / 2) * N, out + y * out_stride, N, log2g, tw, blockIdx.x, smraw,
+                                    Fp32Fft(), crop);
 }
 
 // Filter preparation on its own (the same values rows_fwd_body writes with

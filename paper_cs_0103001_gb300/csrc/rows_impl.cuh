@@ -36,9 +36,8 @@ template <int M> struct RowCfg {
     // (32-byte runs of complex64 per column)
     static constexpr int PPC = (512 / T) > 2 ? 512 / T : 2;
     static constexpr int THREADS = PPC * T;  // 512, or 1024 for M = 8192
-    static constexpr int SR = 2 * PPC + 1;            // staging row stride (odd: no bank conflicts)
     static constexpr int EXCH = PPC * padded_len(M);  // one exchange buffer per pair
-    static constexpr int STAGE = (M / 2) * SR;        // the inverse pass's staging of its slots
+    static constexpr int STAGE = (M / 2) * 2 * PPC;   // the inverse pass's staging of its slots
     static constexpr size_t SMEM_FWD = (size_t)EXCH * sizeof(float2);
     static constexpr size_t SMEM = (size_t)(EXCH > STAGE ? EXCH : STAGE) * sizeof(float2);
 };
@@ -167,12 +166,22 @@ __device__ __forceinline__ void rows_fwd_body(const float *__restrict__ img, flo
 // One block's share of the inverse row pass: spec [M/2][N] (slot order) of one
 // image -> rows of pairs bx*G .. bx*G + G - 1 of out [N][M], unscaled.
 // With PAD, only the crop.rows x crop.cols sub-image is written (pitch crop.cols).
-template <int M, typename FFT = Fp32FftTw15, bool PAD = false>
+// Staging of the inverse row pass: column k's 2G slots in row k (no padding);
+// slot s of row k sits at s ^ h(k), an XOR of the low bits that spreads the
+// reads of one slot for 16 consecutive k (a half warp) over all 16 bank
+// pairs: h(k) = (k >> max(0, 3 - log2 G)) mod min(2G, 16).
+__device__ __forceinline__ int stage_pos(int k, int s, int log2g) {
+    const int sh = log2g < 3 ? 3 - log2g : 0;
+    const int m = (log2g < 3 ? (2 << log2g) : 16) - 1;
+    return (k << (log2g + 1)) + (s ^ ((k >> sh) & m));
+}
+
+template <int M, typename FFT = Fp32Fft, bool PAD = false>
 __device__ __forceinline__ void rows_inv_body(const float2 *__restrict__ spec, float *__restrict__ out, int N,
                                               int log2g, const float2 *__restrict__ tw, int bx,
                                               unsigned char *smraw, FFT fft = FFT(), Crop crop = Crop{0, 0}) {
     typedef RowCfg<M> K;
-    constexpr int E = K::E, T = K::T, SR = K::SR, H2 = M / 2;
+    constexpr int E = K::E, T = K::T, H2 = M / 2;
     float2 *sm = reinterpret_cast<float2 *>(smraw);
     const int G = 1 << log2g;
     const int g = threadIdx.x / T;
@@ -189,8 +198,8 @@ __device__ __forceinline__ void rows_inv_body(const float2 *__restrict__ spec, f
         for (int idx = threadIdx.x; idx < n; idx += K::THREADS) {
             const int k = idx >> log2g, s = (idx & (G - 1)) * 2;
             const float4 x = *reinterpret_cast<const float4 *>(sb + (size_t)k * N + s);
-            stg[k * SR + s] = make_float2(x.x, x.y);
-            stg[k * SR + s + 1] = make_float2(x.z, x.w);
+            stg[stage_pos(k, s, log2g)] = make_float2(x.x, x.y);
+            stg[stage_pos(k, s + 1, log2g)] = make_float2(x.z, x.w);
         }
     }
     __syncthreads();
@@ -201,18 +210,18 @@ __device__ __forceinline__ void rows_inv_body(const float2 *__restrict__ spec, f
             const int k = t + T * e;
             float2 A, B;
             if (e < E / 2) {  // 0 <= k < M/2
-                A = stg[k * SR + g];
-                B = stg[k * SR + G + g];
+                A = stg[stage_pos(k, g, log2g)];
+                B = stg[stage_pos(k, G + g, log2g)];
                 if (e == 0 && t == 0) {
                     A.y = 0.f;
                     B.y = 0.f;
                 }
             } else if (e == E / 2 && t == 0) {  // k = M/2: the packed Nyquist bins
-                A = make_float2(stg[g].y, 0.f);
-                B = make_float2(stg[G + g].y, 0.f);
+                A = make_float2(stg[stage_pos(0, g, log2g)].y, 0.f);
+                B = make_float2(stg[stage_pos(0, G + g, log2g)].y, 0.f);
             } else {  // M/2 < k < M: A[k] = conj A[M-k]
                 const int km = M - k;
-                const float2 am = stg[km * SR + g], bm = stg[km * SR + G + g];
+                const float2 am = stg[stage_pos(km, g, log2g)], bm = stg[stage_pos(km, G + g, log2g)];
                 A = make_float2(am.x, -am.y);
                 B = make_float2(bm.x, -bm.y);
             }
