@@ -115,8 +115,8 @@ template <int M>
 __global__ void __launch_bounds__(RowCfg<M>::THREADS, RowCfg<M>::THREADS <= 512 ? 2 : 1)
     k_rows_fwd_tma(const float *__restrict__ img, float2 *__restrict__ spec, int N, int log2g,
                    const float2 *__restrict__ tw, const __grid_constant__ CUtensorMap omap) {
-    extern __shared__ __align__(128) unsigned char smraw[];
-    unsigned char *base = smraw + ((128u - (smem_u32(smraw) & 127u)) & 127u);  // TMA wants 128-byte alignment
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    unsigned char *base = smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u);  // the box's swizzle period
     const size_t y = blockIdx.y;
     rows_fwd_body<M, Fp32Fft, false, true>(img + y * N * M, spec + y * (M / 2) * N, N, log2g, tw, blockIdx.x, base,
                                            Fp32Fft(), Crop{0, 0}, &omap, (int)y);
@@ -134,7 +134,7 @@ static bool spec_map(CUtensorMap *map, void *spec, int rows, int cols, int nimg,
     cuuint32_t box[3] = {(cuuint32_t)(4 * g), (cuuint32_t)(h2 < 256 ? h2 : 256), 1};
     cuuint32_t estr[3] = {1, 1, 1};
     return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, spec, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+               g == 2 ? CU_TENSOR_MAP_SWIZZLE_32B : CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -145,7 +145,7 @@ static cudaError_t run_rows_fwd(const float *img, void *spec, int rows, int nimg
         const int lg = log2_pairs_per_block(rows, M);
         CUtensorMap map;
         if ((1 << lg) == K::PPC && spec_map(&map, spec, rows, M, nimg, K::PPC)) {
-            const size_t smem = K::SMEM_FWD + 128;
+            const size_t smem = K::SMEM_FWD + 1024;
             cudaError_t e = set_smem<M>((const void *)k_rows_fwd_tma<M>, smem);
             if (e != cudaSuccess) return e;
             dim3 grid((rows / 2) >> lg, nimg);

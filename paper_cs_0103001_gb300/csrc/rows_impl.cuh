@@ -58,17 +58,31 @@ __device__ __forceinline__ float2 split_ab(const float2 *exg, int k, bool side) 
                 : make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
 }
 
+// A[k] and B[k] of a row pair at once (two reads of the exchange buffer).
+template <int M>
+__device__ __forceinline__ void split_both(const float2 *exg, int k, float2 &A, float2 &B) {
+    const float2 zk = exg[pad16(k)];
+    const float2 zm = exg[pad16(k == 0 ? M / 2 : M - k)];
+    if (k == 0) {
+        A = make_float2(zk.x, zm.x);
+        B = make_float2(zk.y, zm.y);
+    } else {
+        A = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+        B = make_float2(0.5f * (zk.y + zm.y), 0.5f * (zm.x - zk.x));
+    }
+}
+
 // One block's share of the forward row pass: row pairs bx*G .. bx*G + G - 1 of
 // one image.  img: the image [N][M]; spec: its half spectra [M/2][N] (slot
 // order).  Every thread of the block must call it; it ends after a
 // block-wide barrier-free epilogue, so a caller that reuses shared memory
 // must synchronise first.
 // With PAD, img is the crop.rows x crop.cols sub-image (pitch crop.cols) and
-// the rest of the grid reads as zero.  With TSTORE (G >= 2) the block's run
-// of 2G slots of every column is gathered in shared memory as the dense box
+// the rest of the grid reads as zero.  With TSTORE (G = PPC >= 2) the block's
+// run of 2G slots of every column is gathered in shared memory as the box
 // [k][2G] and leaves by tensor stores through omap (a 3D view {2N floats,
-// M/2 columns, images} of the half spectra) at image z; smraw is then
-// 128-byte aligned.
+// M/2 columns, images} of the half spectra, with the 32-byte swizzle when
+// PPC = 2) at image z; smraw is then 1024-byte aligned.
 template <int M, typename FFT = Fp32Fft, bool PAD = false, bool TSTORE = false>
 __device__ __forceinline__ void rows_fwd_body(const float *__restrict__ img, float2 *__restrict__ spec, int N,
                                               int log2g, const float2 *__restrict__ tw, int bx,
@@ -114,7 +128,40 @@ __device__ __forceinline__ void rows_fwd_body(const float *__restrict__ img, flo
     // consecutive slots s, s + 1 of the block's run of 2G (s < G: A of pairs
     // s, s + 1; s >= G: B of pairs s - G, s - G + 1), 16 bytes per store
     float2 *sb = spec + (size_t)bx * 2 * G;
-    if constexpr (TSTORE) {
+    if constexpr (TSTORE && K::PPC == 2) {
+        // two pairs: each thread takes whole columns k (4 of them), reads
+        // Z0[k], Z0[M-k], Z1[k], Z1[M-k] once for the four outputs A0 A1 B0 B1,
+        // and writes them as the two 16-byte chunks of box row k.  The box is
+        // stored with the 32-byte swizzle (chunk c of row k at c ^ ((k / 4) mod
+        // 2)), so the eight rows a quarter warp writes cover all 32 banks.
+        constexpr int CPT = H2 / K::THREADS;
+        static_assert(CPT * K::THREADS == H2, "whole columns per thread");
+        float4 out[2 * CPT];
+#pragma unroll
+        for (int i = 0; i < CPT; ++i) {
+            const int k = threadIdx.x + i * K::THREADS;
+            float2 a0, b0, a1, b1;
+            split_both<M>(sm, k, a0, b0);
+            split_both<M>(sm + padded_len(M), k, a1, b1);
+            out[2 * i] = make_float4(a0.x, a0.y, a1.x, a1.y);
+            out[2 * i + 1] = make_float4(b0.x, b0.y, b1.x, b1.y);
+        }
+        __syncthreads();  // every read of the exchange buffers is complete
+        float4 *box = reinterpret_cast<float4 *>(sm);
+#pragma unroll
+        for (int i = 0; i < CPT; ++i) {
+            const int k = threadIdx.x + i * K::THREADS, f = (k >> 2) & 1;
+            box[2 * k + f] = out[2 * i];
+            box[2 * k + (f ^ 1)] = out[2 * i + 1];
+        }
+        fence_async_smem();
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            for (int k0 = 0; k0 < H2; k0 += 256) tma_store_3d(omap, bx * 8, k0, z, sm + (size_t)k0 * 4);
+            bulk_commit();
+            bulk_wait_read();
+        }
+    } else if constexpr (TSTORE) {
         // every unit (k, s) of the block, K::UNITS per thread, into registers;
         // then into the box [k][2G] over the exchange buffers (16-byte stores,
         // consecutive units adjacent) and out by the TMA
