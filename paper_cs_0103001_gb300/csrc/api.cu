@@ -558,7 +558,7 @@ static int pipeline_chunk(gbfft_plan *p, const float *img, const float *H, float
     return launch(p, GBFFT_STAGE_ROWS_INV, s, [&] {
         if (cropped) return launch_rows_pad(false, spec, out, rows, cols, nb, crop_r, crop_c, tw, s);
         return terms ? launch_rows_tc(false, spec, out, rows, cols, nb, tw, terms, s)
-                     : launch_rows_inv(spec, out, rows, cols, nb, tw, s);
+                     : launch_rows_inv(spec, out, rows, cols, nb, tw, reinterpret_cast<int *>(p->ws + p->off_status), s);
     });
 }
 
@@ -628,7 +628,8 @@ int fft2_filter_ifft2_analytic(gbfft_plan_t p, const float *img, int kind, doubl
         });
         if (rc) return rc;
         rc = launch(p, GBFFT_STAGE_ROWS_INV, s, [&] {
-            return launch_rows_inv(spec, out + b0 * np, rows, cols, nb, p->ws + p->off_tw0, s);
+            return launch_rows_inv(spec, out + b0 * np, rows, cols, nb, p->ws + p->off_tw0,
+                                   reinterpret_cast<int *>(p->ws + p->off_status), s);
         });
         if (rc) return rc;
     }
@@ -721,7 +722,8 @@ int fft2_filter_ifft2_backward(gbfft_plan_t p, const float *img, const float *H,
         if (rc) return rc;
         if (grad_img) {
             rc = launch(p, GBFFT_STAGE_ROWS_INV, s, [&] {
-                return launch_rows_inv(spec_g, grad_img + b0 * np, rows, cols, nb, p->ws + p->off_tw0, s);
+                return launch_rows_inv(spec_g, grad_img + b0 * np, rows, cols, nb, p->ws + p->off_tw0,
+                                       reinterpret_cast<int *>(p->ws + p->off_status), s);
             });
             if (rc) return rc;
         }

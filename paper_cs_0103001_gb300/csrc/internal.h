@@ -89,7 +89,7 @@ cudaError_t launch_cols_analytic(void *spec, int kind, double p0, double p1, int
 cudaError_t launch_cols_filter(void *spec, const float *hs, const float *beta, long long hs_img, long long beta_img,
                                int rows, int cols, int nimg, const void *tw_rows, int *status, cudaStream_t s);
 cudaError_t launch_rows_inv(const void *spec, float *out, int rows, int cols, int nimg, const void *tw_cols,
-                            cudaStream_t s);
+                            int *status, cudaStream_t s);
 // Tensor-core variants (tc2d.cu): radix-16 passes as split-BF16 DFT-matrix
 // products with `terms` = 2 or 3 BF16 parts per operand; sides 512..4096.
 bool tc_supported(int rows, int cols);

@@ -100,7 +100,7 @@ extern "C" int fft2_filter_ifft2_noalloc(int64_t rows, int64_t cols, int64_t bat
                                    (float)(1.0 / (double)np), 0, 0, 0, s);
         if (e == cudaSuccess) e = launch_rows_fwd(img + b * np, spec, (int)rows, (int)cols, 1, tw_c, s);
         if (e == cudaSuccess) e = launch_cols_filter(spec, hs, beta, 0, 0, (int)rows, (int)cols, 1, tw_r, nullptr, s);
-        if (e == cudaSuccess) e = launch_rows_inv(spec, out + b * np, (int)rows, (int)cols, 1, tw_c, s);
+        if (e == cudaSuccess) e = launch_rows_inv(spec, out + b * np, (int)rows, (int)cols, 1, tw_c, nullptr, s);
         if (e != cudaSuccess) return GBFFT_ERR_CUDA;
     }
     return GBFFT_OK;

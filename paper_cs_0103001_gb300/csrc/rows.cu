@@ -163,9 +163,37 @@ static cudaError_t run_rows_fwd(const float *img, void *spec, int rows, int nimg
     return cudaGetLastError();
 }
 
+// The inverse row pass with its slot runs arriving by tensor loads
+// (rows_inv_body with TLOAD): two pairs per block.
 template <int M>
-static cudaError_t run_rows_inv(const void *spec, float *out, int rows, int nimg, const void *tw, cudaStream_t s) {
+__global__ void __launch_bounds__(RowCfg<M>::THREADS, 2)
+    k_rows_inv_tma(float *__restrict__ out, int N, int log2g, const float2 *__restrict__ tw,
+                   const __grid_constant__ CUtensorMap imap, int *status) {
+    extern __shared__ __align__(1024) unsigned char smraw[];
+    unsigned char *base = smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u);  // the box's swizzle period
+    uint64_t *bar = reinterpret_cast<uint64_t *>(base + RowCfg<M>::SMEM);
+    const size_t y = blockIdx.y;
+    rows_inv_body<M, Fp32Fft, false, true>(nullptr, out + y * N * M, N, log2g, tw, blockIdx.x, base, Fp32Fft(),
+                                           Crop{0, 0}, &imap, (int)y, bar, status);
+}
+
+template <int M>
+static cudaError_t run_rows_inv(const void *spec, float *out, int rows, int nimg, const void *tw, int *status,
+                                cudaStream_t s) {
     typedef RowCfg<M> K;
+    if constexpr (K::PPC == 2 && K::THREADS <= 512) {
+        const int lg = log2_pairs_per_block(rows, M);
+        CUtensorMap map;
+        if (status && (1 << lg) == 2 && spec_map(&map, const_cast<void *>(spec), rows, M, nimg, 2)) {
+            const size_t smem = K::SMEM + 1024 + 16;
+            cudaError_t e = set_smem<M>((const void *)k_rows_inv_tma<M>, smem);
+            if (e != cudaSuccess) return e;
+            dim3 grid((rows / 2) >> lg, nimg);
+            k_rows_inv_tma<M><<<grid, K::THREADS, smem, s>>>(out, rows, lg, static_cast<const float2 *>(tw), map,
+                                                             status);
+            return cudaGetLastError();
+        }
+    }
     cudaError_t e = set_smem<M>((const void *)k_rows_inv<M>, K::SMEM);
     if (e != cudaSuccess) return e;
     const int lg = log2_pairs_per_block(rows, M);
@@ -221,10 +249,10 @@ cudaError_t launch_rows_fwd(const float *img, void *spec, int rows, int cols, in
 }
 
 cudaError_t launch_rows_inv(const void *spec, float *out, int rows, int cols, int nimg, const void *tw_cols,
-                            cudaStream_t s) {
+                            int *status, cudaStream_t s) {
     switch (ilog2(cols)) {
 #define GBFFT_CASE(L) \
-    case L: return run_rows_inv<(1 << L)>(spec, out, rows, nimg, tw_cols, s);
+    case L: return run_rows_inv<(1 << L)>(spec, out, rows, nimg, tw_cols, status, s);
         GBFFT_CASE(1) GBFFT_CASE(2) GBFFT_CASE(3) GBFFT_CASE(4) GBFFT_CASE(5) GBFFT_CASE(6) GBFFT_CASE(7)
         GBFFT_CASE(8) GBFFT_CASE(9) GBFFT_CASE(10) GBFFT_CASE(11) GBFFT_CASE(12) GBFFT_CASE(13)
 #undef GBFFT_CASE

@@ -223,10 +223,17 @@ __device__ __forceinline__ int stage_pos(int k, int s, int log2g) {
     return (k << (log2g + 1)) + (s ^ ((k >> sh) & m));
 }
 
-template <int M, typename FFT = Fp32Fft, bool PAD = false>
+// With TLOAD (PPC = G = 2) the block's run of 2G slots of every column
+// arrives by tensor loads through imap (the forward pass's 3D view of the half
+// spectra, 32-byte swizzle) into the box [k][4] at image z, on the mbarrier
+// bar (bounded wait; a wait that gives up sets *status and the block leaves);
+// smraw is then 1024-byte aligned.
+template <int M, typename FFT = Fp32Fft, bool PAD = false, bool TLOAD = false>
 __device__ __forceinline__ void rows_inv_body(const float2 *__restrict__ spec, float *__restrict__ out, int N,
                                               int log2g, const float2 *__restrict__ tw, int bx,
-                                              unsigned char *smraw, FFT fft = FFT(), Crop crop = Crop{0, 0}) {
+                                              unsigned char *smraw, FFT fft = FFT(), Crop crop = Crop{0, 0},
+                                              const CUtensorMap *imap = nullptr, int z = 0, uint64_t *bar = nullptr,
+                                              int *status = nullptr) {
     typedef RowCfg<M> K;
     constexpr int E = K::E, T = K::T, H2 = M / 2;
     float2 *sm = reinterpret_cast<float2 *>(smraw);
@@ -239,7 +246,31 @@ __device__ __forceinline__ void rows_inv_body(const float2 *__restrict__ spec, f
     rows_of_pair(active ? p : 0, N, a, b);
 
     float2 *stg = sm;
-    {
+    // slot s of column k in the staging: the XOR layout below, or (TLOAD) the
+    // swizzled box: chunk s / 2 of row k at (s / 2) ^ ((k / 4) mod 2)
+    auto spos = [&](int k, int s) {
+        if constexpr (TLOAD)
+            return 4 * k + 2 * ((s >> 1) ^ ((k >> 2) & 1)) + (s & 1);
+        else
+            return stage_pos(k, s, log2g);
+    };
+    if constexpr (TLOAD) {
+        static_assert(K::PPC == 2, "two pairs per block");
+        if (threadIdx.x == 0) {
+            mbar_init(bar, 1);
+            mbar_expect_tx(bar, (uint32_t)(H2 * 4 * sizeof(float2)));
+            for (int k0 = 0; k0 < H2; k0 += 256) tma_load_3d(sm + (size_t)k0 * 4, imap, bx * 8, k0, z, bar);
+        }
+        __syncthreads();  // the barrier is initialised before anyone tests it
+        const bool ok = mbar_wait_bounded(bar, 0, kTmaPolls);
+        if (__syncthreads_or(!ok)) {
+            if (threadIdx.x == 0) {
+                atomicExch(status, 1);
+                mbar_wait_bounded(bar, 0, kTmaPolls);  // the copies in flight, bounded
+            }
+            return;  // uniform
+        }
+    } else {
         const float2 *sb = spec + (size_t)bx * 2 * G;
         const int n = H2 << log2g;
         for (int idx = threadIdx.x; idx < n; idx += K::THREADS) {
@@ -248,8 +279,8 @@ __device__ __forceinline__ void rows_inv_body(const float2 *__restrict__ spec, f
             stg[stage_pos(k, s, log2g)] = make_float2(x.x, x.y);
             stg[stage_pos(k, s + 1, log2g)] = make_float2(x.z, x.w);
         }
+        __syncthreads();
     }
-    __syncthreads();
     float2 v[E];
     if (active) {
 #pragma unroll
@@ -257,18 +288,18 @@ __device__ __forceinline__ void rows_inv_body(const float2 *__restrict__ spec, f
             const int k = t + T * e;
             float2 A, B;
             if (e < E / 2) {  // 0 <= k < M/2
-                A = stg[stage_pos(k, g, log2g)];
-                B = stg[stage_pos(k, G + g, log2g)];
+                A = stg[spos(k, g)];
+                B = stg[spos(k, G + g)];
                 if (e == 0 && t == 0) {
                     A.y = 0.f;
                     B.y = 0.f;
                 }
             } else if (e == E / 2 && t == 0) {  // k = M/2: the packed Nyquist bins
-                A = make_float2(stg[stage_pos(0, g, log2g)].y, 0.f);
-                B = make_float2(stg[stage_pos(0, G + g, log2g)].y, 0.f);
+                A = make_float2(stg[spos(0, g)].y, 0.f);
+                B = make_float2(stg[spos(0, G + g)].y, 0.f);
             } else {  // M/2 < k < M: A[k] = conj A[M-k]
                 const int km = M - k;
-                const float2 am = stg[stage_pos(km, g, log2g)], bm = stg[stage_pos(km, G + g, log2g)];
+                const float2 am = stg[spos(km, g)], bm = stg[spos(km, G + g)];
                 A = make_float2(am.x, -am.y);
                 B = make_float2(bm.x, -bm.y);
             }
