@@ -102,8 +102,9 @@ cudaError_t launch_cols_spectrum(const void *spec, float *mag_T, float *nyq, flo
     }
 }
 
-// ---- The column pass through the TMA (columns of N >= 4096 rows, one per
-// block at a time).  A column's N slots (contiguous, slot order) are viewed
+// ---- The column pass through the TMA (columns of 4096 rows: 256 threads per
+// column, one column per block at a time; taller columns use the
+// one-column-per-block kernel).  A column's N slots (contiguous, slot order) are viewed
 // as N/16 rows of 128 bytes and move as one 2D tensor box with the 128-byte
 // swizzle (the 16-byte chunk c of row r sits at chunk c ^ (r mod 8)), which
 // keeps the threads' slot-order reads and writes free of bank conflicts; the
