@@ -80,16 +80,18 @@ def test_batch_per_image_filter_and_chunks(gb):
     assert max_rel_l2(out.reshape(B, rows, cols), oracle.pipeline(img, H[2]), axes=(1, 2)) <= tol_fp32(rows * cols)
 
 
-@pytest.mark.parametrize("cols,chunk", [(64, 3), (16, 0), (512, 2)])
-def test_tall_batches_through_the_persistent_column_pass(gb, cols, chunk):
-    """Images of 4096 rows take the persistent TMA-fed column pass: batches of
-    several images per launch (columns of consecutive images in one walk),
-    per-image filters, and row-pass groups from 2 to 256 pairs."""
+@pytest.mark.parametrize("rows,cols,chunk", [(4096, 64, 3), (4096, 16, 0), (4096, 512, 2), (2048, 256, 2),
+                                             (2048, 4, 0), (1024, 128, 0), (1024, 8, 3)])
+def test_tall_batches_through_the_persistent_column_pass(gb, rows, cols, chunk):
+    """Batches of tall images, several per launch, with per-image filters and
+    row-pass groups from 2 to 256 pairs: 4096 rows take the persistent
+    TMA-fed column pass (columns of consecutive images in one walk), 1024 and
+    2048 rows the kernel with several columns per block."""
     import torch
 
     from paper_cs_0103001_gb300 import _native as nat
 
-    rows, B = 4096, 3
+    B = 3
     img = np.stack([synth.sky(rows, cols, 60, 16, b) for b in range(B)])
     H = np.stack([synth.random_filter(rows, cols, 17, b) for b in range(B)])
     plan = gb.Plan2D(rows, cols, B, "cuda", {nat.OPT_H_BATCH_STRIDE: rows * cols, nat.OPT_IMAGES_PER_CHUNK: chunk,
