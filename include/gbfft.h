@@ -65,7 +65,7 @@ typedef enum {
     GBFFT_ERR_DTYPE = -3,        /* unknown or unsupported dtype for this call */
     GBFFT_ERR_MISALIGNED = -4,   /* a data pointer is not 16-byte aligned */
     GBFFT_ERR_WORKSPACE = -5,    /* no workspace bound, or the one given is too small */
-    GBFFT_ERR_UNSUPPORTED = -6,  /* valid request this build does not implement */
+    GBFFT_ERR_UNSUPPORTED = -6,  /* valid request the library does not implement */
     GBFFT_ERR_CUDA = -7,         /* a CUDA call or kernel launch failed */
     GBFFT_ERR_TIMEOUT = -8,      /* a bounded device-side wait gave up */
     GBFFT_ERR_INVALID_VALUE = -9 /* bad option key/value or wrong plan kind */
