@@ -7,9 +7,14 @@ log-uniform peak amplitudes 10..1e4, seeded) through a Butterworth low-pass
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl gbfft|reference]
 
-Prints one JSON line (rank 0).  `value` is the pipeline's throughput
-expressed as the bandwidth of its compulsory I/O: 12 bytes per pixel (read
-img and H, write out) divided by the device time per image.  Each step works
+Prints one JSON line (rank 0).  `value` is the pipeline's effective
+bandwidth: the nominal traffic of a three-pass complex-to-complex schedule
+(44 bytes per pixel, the figure the 60 % target is quoted on) divided by the
+device time per image.  The kernels run a half-spectrum schedule that moves
+fewer bytes, so `value` is not achieved bandwidth: `pct_hbm_peak` and the
+`hbm` object give the achieved fractions of the measured HBM copy bandwidth,
+on the schedule's own algorithmic bytes (32 per pixel) and on the DRAM bytes
+ncu counted per kernel (while those records match the kernel sources).  Each step works
 on a freshly flushed L2 (a 256 MiB buffer is written between steps, outside
 the timed events); the per-step device times are summed.  Multi-GPU runs are
 independent replicas (each rank its own image; no collective on the data
@@ -39,12 +44,14 @@ N_SOURCES = 20000
 WORKLOAD = "fft2_butterworth_ifft2_4096x4096_fp32"
 METRIC = "2D FFT→filter→IFFT GB/s & % HBM peak at 4096² fp32, rel-L2 vs FP64 oracle"
 COMPULSORY_BYTES_PER_PX = 12  # img 4 + H 4 + out 4
-# The metric's GB/s counts the nominal traffic of a three-pass complex-to-complex
+# `value` counts the nominal traffic of a three-pass complex-to-complex
 # schedule, 44 bytes per pixel (rows: 4 read + 8 write; columns: 8 read + 4
 # filter + 8 write; inverse rows: 8 read + 4 write), 738.2 MB per 4096^2 image,
 # whatever the implementation actually moves (the effective-bandwidth convention
-# of FFT benchmarks, like the 5 N log2 N flop count).  The compulsory figure
-# (12 bytes per pixel) is reported beside it.
+# of FFT benchmarks, like the 5 N log2 N flop count).  It is an effective
+# figure, not a fraction of HBM: the achieved fractions use the bytes the
+# half-spectrum schedule moves (STAGE_BYTES_PER_PX, 32 per pixel) and the DRAM
+# bytes ncu counted.  The compulsory figure (12 bytes per pixel) is reported too.
 NOMINAL_C2C_BYTES_PER_PX = 44
 METRIC_BYTES_PER_PX = NOMINAL_C2C_BYTES_PER_PX
 # algorithmic bytes per pixel of each stage of the half-spectrum schedule:
@@ -53,6 +60,7 @@ METRIC_BYTES_PER_PX = NOMINAL_C2C_BYTES_PER_PX
 # pass reads spectra (4) and prepared filter (2) and writes spectra (4); the
 # inverse rows read spectra (4) and write out (4)
 STAGE_BYTES_PER_PX = {"rows_fwd": 8, "filter_prep": 6, "cols_filter": 10, "rows_inv": 8}
+SCHEDULE_BYTES_PER_PX = sum(STAGE_BYTES_PER_PX.values())  # 32
 FLOPS_PER_IMAGE = 2 * 5 * ROWS * COLS * math.log2(ROWS * COLS) + 2 * ROWS * COLS
 
 
@@ -341,12 +349,26 @@ def run_gbfft(args):
         dom_bytes = STAGE_BYTES_PER_PX.get(dom, 0) * px
         achieved = dom_bytes / (dom_ms * 1e-3) / 1e9
         traffic = recorded_traffic(dom)
-        # CPU baseline: the FP64 oracle on the same image, all host cores
+        # achieved HBM: the schedule's algorithmic bytes per image, and the
+        # DRAM bytes ncu counted per launch of each stage (when every record
+        # matches the current kernel sources), over the device time per image
+        alg_gbs = world * SCHEDULE_BYTES_PER_PX * px / (ms * 1e-3) / 1e9
+        stage_traffic = {k: recorded_traffic(k) for k in STAGE_BYTES_PER_PX}
+        dram_step = sum(stage_traffic.values()) if all(v is not None for v in stage_traffic.values()) else None
+        dram_gbs = world * dram_step / (ms * 1e-3) / 1e9 if dram_step is not None else None
+        # CPU baseline: the FP64 oracle on the same image, all host cores, then
+        # one thread
         import oracle
 
         t0 = time.perf_counter()
         ref = oracle.pipeline(img_np, H_np)
         cpu_s = time.perf_counter() - t0
+        cores = oracle.max_threads()
+        oracle.set_threads(1)
+        t0 = time.perf_counter()
+        oracle.pipeline(img_np, H_np)
+        cpu1_s = time.perf_counter() - t0
+        oracle.set_threads(cores)
         got = out.cpu().numpy().astype(np.float64)
         rel = float(np.linalg.norm(got - ref) / np.linalg.norm(ref))
         tol = 2e-7 * math.log2(px)
@@ -367,7 +389,19 @@ def run_gbfft(args):
                        "sources": N_SOURCES, "filter": "butterworth order 4, cutoff 0.1 Nyquist",
                        "l2": "flushed between steps (256 MiB write outside the timed events)",
                        "parallelism": f"replicas x{world}"},
-            "pct_hbm_peak": round(100.0 * value / (world * peak), 2),
+            "value_basis": "effective GB/s: nominal 44 B/px of a three-pass C2C schedule (738.2 MB per image) "
+                           "over the device time; not achieved bandwidth",
+            "pct_hbm_peak": round(100.0 * alg_gbs / (world * peak), 2),
+            "hbm": {"peak_gbs": peak, "peak_kind": peak_kind,
+                    "algorithmic_bytes_per_px": SCHEDULE_BYTES_PER_PX,
+                    "achieved_gbs_algorithmic": round(alg_gbs, 1),
+                    "frac_algorithmic": round(alg_gbs / (world * peak), 4),
+                    "dram_bytes_per_image_ncu": dram_step,
+                    "achieved_gbs_dram": round(dram_gbs, 1) if dram_gbs is not None else None,
+                    "frac_dram": round(dram_gbs / (world * peak), 4) if dram_gbs is not None else None,
+                    "effective_gbs_nominal_44Bpx": round(value, 1),
+                    "note": "pct_hbm_peak = frac_algorithmic; frac_dram uses the ncu DRAM bytes of each stage "
+                            "(profiles/dram_traffic.txt, null once a kernel changed since its capture)"},
             "us_per_image": round(ms * 1e3, 2),
             "images_per_s": round(world * 1e3 / ms, 1),
             "gflops_5nlogn": round(world * FLOPS_PER_IMAGE / (ms * 1e-3) / 1e9, 1),
@@ -383,9 +417,11 @@ def run_gbfft(args):
                          "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
                          "traffic": traffic, "algorithmic_bytes": dom_bytes},
             "cpu_baseline": {"value": round(METRIC_BYTES_PER_PX * px / cpu_s / 1e9, 4), "unit": "GB/s",
-                             "cores": oracle.max_threads(), "kind": "oracle",
+                             "cores": cores, "kind": "oracle",
                              "sample": "one 4096x4096 image through the FP64 C oracle pipeline",
-                             "seconds": round(cpu_s, 3)},
+                             "seconds": round(cpu_s, 3),
+                             "one_thread": {"value": round(METRIC_BYTES_PER_PX * px / cpu1_s / 1e9, 4),
+                                            "seconds": round(cpu1_s, 3), "cores": 1}},
             "e2e": {"value": round(world * METRIC_BYTES_PER_PX * px / (e2e_ms * 1e-3) / 1e9, 1), "unit": "GB/s",
                     "ms_per_step": round(e2e_ms, 4), "h2d_bytes_per_step": 4 * px, "d2h_bytes_per_step": 4 * px,
                     "steps": e_steps, "copies_only_ms_per_step": round(copy_ms, 4),

@@ -241,8 +241,9 @@ int fft2_filter_ifft2_backward(gbfft_plan_t plan, const float *img, const float 
 
 /* Allocation-free form of fft2_filter_ifft2 (the paper has no counterpart;
  * it exists for callers that cannot allocate device memory while running:
- * code inside CUDA graph capture, hosts that own every device allocation,
- * loops that must not call cudaMalloc because it can block or synchronise).
+ * loops that must not call cudaMalloc because it can block or synchronise
+ * the device, and plugins whose host application owns every device
+ * allocation and passes them only their inputs and outputs).
  * Same result as fft2_filter_ifft2 for `batch` float32 images of
  * rows x cols (row-major); image b uses filter H + b * h_batch_stride
  * (0 = one shared filter).  No plan and no workspace: the scratch memory is a
@@ -250,12 +251,14 @@ int fft2_filter_ifft2_backward(gbfft_plan_t plan, const float *img, const float 
  * that loads the library until the process exits).
  *   - rows, cols powers of two >= 2 with rows * cols <= 2048 * 2048; larger
  *     images return GBFFT_ERR_INVALID_SIZE.
- *   - The first call on a device looks the array up (cudaGetSymbolAddress
- *     with that device current): make that first call before any stream
- *     capture.  A call whose shape differs from the previous call on the
- *     device regenerates the twiddle tables on `stream`.
+ *   - The first call on a device sets that device up (with that device
+ *     current): it looks the array up with cudaGetSymbolAddress, writes the
+ *     twiddle tables of every length into it on `stream` and waits for
+ *     them (cudaStreamSynchronize).  Make that first call before any stream
+ *     capture.  Later calls never rewrite the tables.
  *   - All calls share the array and it keeps the last call's contents:
  *     calls that overlap on the GPU (other streams, unordered threads) race.
+ *     Nothing in it needs to start at zero.
  *   - Allocates nothing: no cudaMalloc, cudaFree or allocating library call. */
 int fft2_filter_ifft2_noalloc(int64_t rows, int64_t cols, int64_t batch, const float *img, const float *H,
                               int64_t h_batch_stride, float *out, gbfft_stream_t stream);

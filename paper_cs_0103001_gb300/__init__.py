@@ -8,24 +8,23 @@ application (Sec. 5), as hand-written CUDA kernels behind a C ABI
 (include/gbfft.h, libgbfft.so).  PyTorch is used for device memory and
 streams only.
 
-Importing this package loads libgbfft.so and fails if it is missing; build it
-with ``paper_cs_0103001_gb300.build.build()``.
+The transforms load libgbfft.so on first use (the first attribute taken from
+this package other than ``synth``) and raise if it is missing; build it with
+``paper_cs_0103001_gb300.build.build()``.  ``synth`` (seeded input
+generators, no transform arithmetic) imports without the library, so a
+process that only generates inputs maps no CUDA code.
 """
 
-from .api import (  # noqa: F401
-    Plan1D,
-    Plan2D,
-    Plan2DBatched,
-    clear_plan_cache,
-    fft,
-    fft2_filter_ifft2,
-    fft2_filter_ifft2_analytic,
-    fft2_filter_ifft2_batched,
-    fft2_filter_ifft2_padded,
-    fft2_spectrum,
-    ifft,
-)
+import importlib
 
 __all__ = ["fft", "ifft", "fft2_filter_ifft2", "fft2_filter_ifft2_analytic", "fft2_filter_ifft2_batched",
-           "fft2_filter_ifft2_padded",
-           "fft2_spectrum", "Plan1D", "Plan2D", "Plan2DBatched", "clear_plan_cache"]
+           "fft2_filter_ifft2_padded", "fft2_spectrum", "Plan1D", "Plan2D",
+           "Plan2DBatched", "clear_plan_cache"]
+
+
+def __getattr__(name):
+    if name in __all__:
+        return getattr(importlib.import_module(".api", __name__), name)
+    if name in ("api", "_native"):
+        return importlib.import_module("." + name, __name__)
+    raise AttributeError(f"module {__name__!r} has no attribute {name!r}")

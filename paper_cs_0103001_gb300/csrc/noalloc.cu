@@ -4,21 +4,24 @@
 // between its three kernels) that the caller allocates and binds.  Some
 // callers cannot do that: code that must not call cudaMalloc once it is
 // running (real-time or embedded loops, where an allocation can block or
-// synchronise the device), plugins whose host application owns all device
-// memory, and code recorded into a CUDA graph, where cudaMalloc is not
-// allowed.  fft2_filter_ifft2_noalloc gives them the same result with no
-// workspace argument: its scratch is a fixed, file-scope __device__ array that
-// lives in the library image, so the call allocates nothing.
+// synchronise the device), and plugins whose host application owns all device
+// memory and hands them only their input and output buffers.
+// fft2_filter_ifft2_noalloc gives them the same result with no workspace
+// argument: its scratch is a fixed, file-scope __device__ array that lives in
+// the library image, so the call allocates nothing.
 //
 // Costs and rules (also stated in gbfft.h):
 //  - every GPU that loads the library holds kScratchBytes (about 24.2 MiB)
 //    of device memory for this array until the process exits, used or not;
 //  - rows * cols is limited to kMaxPixels; larger images are rejected;
+//  - the first call on a device sets that device up: it looks the array up
+//    and writes the twiddle tables of every supported length into it (on the
+//    caller's stream, then waits for them); later calls only read the tables;
 //  - all calls share the one array: calls whose work overlaps on the GPU
 //    (different streams, or different host threads without ordering) race;
 //  - the array keeps the previous call's contents; nothing here needs to
 //    start at zero (spectra and prepared filter are fully rewritten by every
-//    call, the twiddle tables whenever the image shape changes).
+//    call, and the tables never change after set-up).
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -29,18 +32,21 @@
 namespace {
 
 constexpr long long kMaxPixels = 2048ll * 2048ll;               // rows * cols
-constexpr size_t kTwiddleBytes = 2 * 8192 * 8;                   // cols + rows tables, complex64
+// twiddle tables of every length n = 2 .. 8192 (n - 1 complex64 entries each),
+// the table of length n at entry n: [n, 2n) for powers of two never overlap
+constexpr size_t kTwiddleBytes = 2 * 8192 * 8;
 constexpr size_t kFilterBytes = (size_t)kMaxPixels / 2 * 4;      // prepared filter, float32
 constexpr size_t kBetaBytes = 8192 * 4;                          // packed-column coefficients
 constexpr size_t kSpectrumBytes = (size_t)kMaxPixels / 2 * 8;    // half spectra, complex64
 constexpr size_t kScratchBytes = kTwiddleBytes + kFilterBytes + kBetaBytes + kSpectrumBytes;  // ~24.2 MiB
 
+static_assert(kTwiddleBytes >= 2 * (size_t(1) << gbfft::kMax2DLog2) * 8, "one table per length up to the 2D maximum");
+
 __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
 struct DeviceState {
-    unsigned char *base = nullptr;  // device address of g_scratch on this device
-    int tw_rows = 0, tw_cols = 0;   // shape whose twiddles the array holds
+    unsigned char *base = nullptr;  // device address of g_scratch on this device, once set up
 };
 DeviceState g_dev[kMaxDevices];
 std::mutex g_mu;
@@ -72,27 +78,24 @@ extern "C" int fft2_filter_ifft2_noalloc(int64_t rows, int64_t cols, int64_t bat
     DeviceState &st = g_dev[dev];
     if (!st.base) {
         // first call on this device (the current one): look up where the
-        // array lives; the host-side symbol itself is not a device address
+        // array lives (the host-side symbol itself is not a device address),
+        // then write every length's twiddle table and wait for them, so that
+        // calls on any stream can read them afterwards
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_scratch);
         if (e != cudaSuccess || !p) return GBFFT_ERR_CUDA;
-        st.base = static_cast<unsigned char *>(p);
+        unsigned char *base = static_cast<unsigned char *>(p);
+        for (int n = 2; n <= (1 << kMax2DLog2) && e == cudaSuccess; n *= 2)
+            e = launch_twiddles(base + (size_t)n * 8, n, false, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return GBFFT_ERR_CUDA;
+        st.base = base;
     }
-    unsigned char *tw_c = st.base;               // row transforms: length cols
-    unsigned char *tw_r = st.base + 8192 * 8;    // column transforms: length rows
+    const unsigned char *tw_c = st.base + (size_t)cols * 8;  // row transforms: length cols
+    const unsigned char *tw_r = st.base + (size_t)rows * 8;  // column transforms: length rows
     float *hs = reinterpret_cast<float *>(st.base + kTwiddleBytes);
     float *beta = reinterpret_cast<float *>(st.base + kTwiddleBytes + kFilterBytes);
     unsigned char *spec = st.base + kTwiddleBytes + kFilterBytes + kBetaBytes;
-    if (st.tw_rows != rows || st.tw_cols != cols) {
-        e = launch_twiddles(tw_c, (int)cols, false, s);
-        if (e == cudaSuccess) e = launch_twiddles(tw_r, (int)rows, false, s);
-        if (e != cudaSuccess) {
-            st.tw_rows = st.tw_cols = 0;
-            return GBFFT_ERR_CUDA;
-        }
-        st.tw_rows = (int)rows;
-        st.tw_cols = (int)cols;
-    }
     const long long np = rows * cols;
     for (long long b = 0; b < batch; ++b) {
         if (b == 0 || h_batch_stride != 0)  // prepare each filter once
