@@ -263,6 +263,46 @@ int fft2_filter_ifft2_backward(gbfft_plan_t plan, const float *img, const float 
 int fft2_filter_ifft2_noalloc(int64_t rows, int64_t cols, int64_t batch, const float *img, const float *H,
                               int64_t h_batch_stride, float *out, gbfft_stream_t stream);
 
+/* ---- one image decomposed over ranks (row slabs) ---------------------------
+ *
+ * The paper spreads its transform over 2^l processes, each computing its share
+ * before the processes exchange results (Sec. 2, cost model Eq. multi /
+ * Table 1).  These calls split one image of fft2_filter_ifft2 over `nranks`
+ * ranks (one GPU each, or emulated on one GPU) by rows instead, with two
+ * exchanges and no other communication:
+ *   1. fft2_slab_rows_forward: rank r transforms its rows into `send`;
+ *   2. exchange 1: chunk q of every rank's `send` goes to rank q, where the
+ *      chunks arrive in rank order as `recv` (an all-to-all of equal chunks);
+ *   3. fft2_slab_columns: rank r filters its block of spectrum columns in
+ *      `recv` in place (column FFT, x s.Hs, column IFFT);
+ *   4. exchange 2: chunk q of every rank's `recv` goes back to rank q, arriving
+ *      in rank order as `back` (the same all-to-all);
+ *   5. fft2_slab_rows_inverse: rank r writes its rows of `out`.
+ * The exchanges are the caller's (e.g. NCCL all-to-all); every buffer holds
+ * fft2_slab_exchange_elems() complex64 values, split into nranks equal
+ * contiguous chunks.  The result equals fft2_filter_ifft2 on the whole image.
+ *
+ * Rank r owns the row pairs (p, rows - p) for p in [r P, (r + 1) P), P =
+ * rows / (2 nranks) (pair 0 is rows 0 and rows/2): its rows are two runs,
+ * [rP, (r+1)P) and the mirrors.  Its columns are the half-spectrum columns
+ * [r C, (r + 1) C), C = cols / (2 nranks).  `img` and `out` are whole
+ * rows x cols float32 images in the rank's memory; only the rank's own rows
+ * are read and written.  rows, cols powers of two, cols >= 4, nranks a power
+ * of two with P a positive multiple of the row pass's pairs per block (2 for
+ * cols >= 256) and C >= 1, else GBFFT_ERR_INVALID_SIZE; rank outside
+ * [0, nranks): GBFFT_ERR_INVALID_VALUE.  The plan's workspace (twiddles and
+ * the rank's share of the prepared filter) is bound as usual. */
+int fft2_slab_plan_create(int64_t rows, int64_t cols, int nranks, int rank, gbfft_plan_t *out);
+/* Complex64 elements in each exchange buffer: (cols/2) x (rows/nranks). */
+int fft2_slab_exchange_elems(gbfft_plan_t plan, int64_t *count);
+/* Step 1: rows of this rank -> send, laid out [cols/2][rows/nranks]. */
+int fft2_slab_rows_forward(gbfft_plan_t plan, const float *img, void *send, gbfft_stream_t stream);
+/* Step 3: recv ([nranks][C][rows/nranks], chunk q from rank q) filtered in
+ * place with H (rows x cols float32, the whole filter, on every rank). */
+int fft2_slab_columns(gbfft_plan_t plan, void *recv, const float *H, gbfft_stream_t stream);
+/* Step 5: back ([cols/2][rows/nranks], as step 1 wrote it) -> this rank's rows of out. */
+int fft2_slab_rows_inverse(gbfft_plan_t plan, const void *back, float *out, gbfft_stream_t stream);
+
 /* Batched plan for the Sec. 5 pipeline over `count` images of uneven sizes,
  * image i being rows[i] x cols[i] (powers of two, 16 <= rows, cols <= 4096),
  * each with its own filter of the same shape.  All images' spectra live in

@@ -11,20 +11,21 @@ streams only.
 The transforms load libgbfft.so on first use (the first attribute taken from
 this package other than ``synth``) and raise if it is missing; build it with
 ``paper_cs_0103001_gb300.build.build()``.  ``synth`` (seeded input
-generators, no transform arithmetic) imports without the library, so a
-process that only generates inputs maps no CUDA code.
+generators, no transform arithmetic) and ``slab`` (index maps of the row-slab
+decomposition) import without the library, so a process that only generates
+inputs maps no CUDA code.
 """
 
 import importlib
 
 __all__ = ["fft", "ifft", "fft2_filter_ifft2", "fft2_filter_ifft2_analytic", "fft2_filter_ifft2_batched",
-           "fft2_filter_ifft2_padded", "fft2_spectrum", "Plan1D", "Plan2D",
-           "Plan2DBatched", "clear_plan_cache"]
+           "fft2_filter_ifft2_padded", "fft2_filter_ifft2_sharded", "fft2_spectrum", "Plan1D", "Plan2D",
+           "Plan2DBatched", "Plan2DSlab", "clear_plan_cache"]
 
 
 def __getattr__(name):
     if name in __all__:
         return getattr(importlib.import_module(".api", __name__), name)
-    if name in ("api", "_native"):
+    if name in ("api", "_native", "slab"):
         return importlib.import_module("." + name, __name__)
     raise AttributeError(f"module {__name__!r} has no attribute {name!r}")

@@ -74,6 +74,11 @@ SIGNATURES = {
     "fft_plan_autotune": (_INT, [_P, _P, _P]),
     "fft_plan_get_option": (_INT, [_P, _INT, ctypes.POINTER(_I64)]),
     "fft2_filter_ifft2_noalloc": (_INT, [_I64, _I64, _I64, _P, _P, _I64, _P, _P]),
+    "fft2_slab_plan_create": (_INT, [_I64, _I64, _INT, _INT, ctypes.POINTER(_P)]),
+    "fft2_slab_exchange_elems": (_INT, [_P, ctypes.POINTER(_I64)]),
+    "fft2_slab_rows_forward": (_INT, [_P, _P, _P, _P]),
+    "fft2_slab_columns": (_INT, [_P, _P, _P, _P]),
+    "fft2_slab_rows_inverse": (_INT, [_P, _P, _P, _P]),
     "gbfft_status_string": (ctypes.c_char_p, [_INT]),
     "gbfft_last_cuda_error": (_INT, []),
     "gbfft_plan_profile_read": (_INT, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64), _INT]),

@@ -219,6 +219,36 @@ class Plan2DBatched(_PlanBase):
         return int(v.value)
 
 
+class Plan2DSlab(_PlanBase):
+    """One rank's share of an image decomposed by rows over `nranks` ranks
+    (include/gbfft.h, fft2_slab_*; the maps are in slab.py).  The three calls
+    run this rank's kernels; the two exchanges between them are the caller's."""
+
+    def __init__(self, rows: int, cols: int, nranks: int, rank: int, device, options=None):
+        h = _P()
+        nat.call("fft2_slab_plan_create", int(rows), int(cols), int(nranks), int(rank), ctypes.byref(h))
+        self.rows, self.cols, self.nranks, self.rank = int(rows), int(cols), int(nranks), int(rank)
+        super().__init__(h, torch.device(device), options)
+        n = ctypes.c_int64()
+        nat.call("fft2_slab_exchange_elems", self.handle, ctypes.byref(n))
+        self.exchange_elems = int(n.value)
+
+    def exchange_buffer(self) -> torch.Tensor:
+        return torch.empty(self.exchange_elems, dtype=torch.complex64, device=self.device)
+
+    def rows_forward(self, img: torch.Tensor, send: torch.Tensor) -> None:
+        with self.lock:
+            nat.call("fft2_slab_rows_forward", self.handle, _ptr(img), _ptr(send), _stream_handle(self.device))
+
+    def columns(self, recv: torch.Tensor, H: torch.Tensor) -> None:
+        with self.lock:
+            nat.call("fft2_slab_columns", self.handle, _ptr(recv), _ptr(H), _stream_handle(self.device))
+
+    def rows_inverse(self, back: torch.Tensor, out: torch.Tensor) -> None:
+        with self.lock:
+            nat.call("fft2_slab_rows_inverse", self.handle, _ptr(back), _ptr(out), _stream_handle(self.device))
+
+
 _cache: dict[tuple, _PlanBase] = {}
 _cache_lock = threading.Lock()
 
@@ -386,3 +416,53 @@ def fft2_filter_ifft2(img: torch.Tensor, H: torch.Tensor) -> torch.Tensor:
     and (for a shared H) in H.
     """
     return _FilterFn.apply(img, H)
+
+
+def fft2_filter_ifft2_sharded(img: torch.Tensor, H: torch.Tensor, group=None, nranks: int | None = None,
+                              out: torch.Tensor | None = None) -> torch.Tensor:
+    """Sec. 5 pipeline on one float32 image [rows, cols] decomposed by rows.
+
+    With a torch.distributed `group` (one rank per GPU, NCCL): every rank
+    passes the whole-image buffers `img` and `out` (only its own rows, see
+    slab.slab_rows, are read and written; the other rows of `out` are left
+    as they are) and the whole filter H; the two exchanges are
+    all_to_all_single calls of equal chunks.  Without a group, `nranks` ranks
+    are emulated on img's device, one after the other, with the exchanges
+    done as local copies; then every row of `out` is written.  Equals
+    fft2_filter_ifft2(img, H).  Not differentiable."""
+    _check_2d(img, H)
+    if img.dim() != 2 or H.shape != img.shape:
+        raise ValueError("one image [rows, cols] and one filter of the same shape")
+    rows, cols = int(img.shape[0]), int(img.shape[1])
+    img, H = img.contiguous(), H.contiguous()
+    if out is None:
+        out = torch.empty_like(img)
+    dev = img.device
+    if group is not None:
+        import torch.distributed as dist
+
+        from . import slab
+
+        R, r = dist.get_world_size(group), dist.get_rank(group)
+        plan = _cached(("slab", rows, cols, R, r, dev), lambda: Plan2DSlab(rows, cols, R, r, dev))
+        send, recv = plan.exchange_buffer(), plan.exchange_buffer()
+        plan.rows_forward(img, send)
+        slab.exchange(send, recv, group)
+        plan.columns(recv, H)
+        slab.exchange(recv, send, group)
+        plan.rows_inverse(send, out)
+        return out
+    R = int(nranks or 1)
+    plans = [_cached(("slab", rows, cols, R, r, dev), lambda r=r: Plan2DSlab(rows, cols, R, r, dev))
+             for r in range(R)]
+    n = plans[0].exchange_elems
+    sends = torch.empty(R, R, n // R, dtype=torch.complex64, device=dev)  # [rank][chunk]
+    for r, p in enumerate(plans):
+        p.rows_forward(img, sends[r])
+    recvs = sends.transpose(0, 1).contiguous()  # rank q receives chunk q of every rank, in rank order
+    for q, p in enumerate(plans):
+        p.columns(recvs[q], H)
+    backs = recvs.transpose(0, 1).contiguous()  # and sends chunk r back to rank r
+    for r, p in enumerate(plans):
+        p.rows_inverse(backs[r], out)
+    return out

@@ -24,7 +24,7 @@ struct ProfRec {
     cudaEvent_t a, b;
 };
 
-enum PlanKind { KIND_1D = 1, KIND_2D = 2, KIND_BATCH = 3 };
+enum PlanKind { KIND_1D = 1, KIND_2D = 2, KIND_BATCH = 3, KIND_SLAB = 4 };
 
 constexpr size_t kAlign = 256;
 size_t align_up(size_t x) { return (x + kAlign - 1) & ~(kAlign - 1); }
@@ -55,6 +55,7 @@ struct gbfft_plan {
     size_t off_status = 0;  // device status word (bounded waits that gave up)
     size_t off_hs = 0, off_beta = 0, off_grad = 0;  // 2D: prepared filter, beta, adjoint sums
     int64_t chunk = 0;           // transforms (1D four-step) or images (2D) per workspace chunk
+    int nranks = 1, rank = 0;    // slab plans: the decomposition and this rank
     int fs_l1 = 0, fs_l2 = 0;    // four-step split
     std::vector<ProfRec> prof;
     // batched plans (KIND_BATCH)
@@ -121,6 +122,21 @@ void layout(gbfft_plan *p) {
     size_t off = 0;
     if (p->kind == KIND_BATCH) {
         layout_batched(p);
+        return;
+    }
+    if (p->kind == KIND_SLAB) {
+        const int64_t rows = int64_t(1) << p->log2r, cols = int64_t(1) << p->log2c;
+        const int64_t mloc = cols / 2 / p->nranks;  // this rank's half-spectrum columns
+        p->off_tw0 = off;  // row transforms (length cols)
+        off = align_up(off + (size_t)cols * 8);
+        p->off_tw1 = off;  // column transforms (length rows)
+        off = align_up(off + (size_t)rows * 8);
+        p->off_hs = off;  // prepared filter of this rank's columns, [mloc][rows]
+        off = align_up(off + (size_t)mloc * rows * 4);
+        p->off_beta = off;
+        off = align_up(off + (size_t)rows * 4);
+        p->off_status = align_up(off);
+        p->need = p->off_status + kAlign;
         return;
     }
     if (p->kind == KIND_1D) {
@@ -450,7 +466,7 @@ int fft_plan_bind_workspace(gbfft_plan_t p, void *workspace, size_t bytes, gbfft
                 return e;
             });
         }
-    } else if (p->kind == KIND_2D) {
+    } else if (p->kind == KIND_2D || p->kind == KIND_SLAB) {
         rc = launch(p, GBFFT_STAGE_TWIDDLES, s, [&] {
             cudaError_t e = launch_twiddles(p->ws + p->off_tw0, 1 << p->log2c, false, s);
             if (e == cudaSuccess) e = launch_twiddles(p->ws + p->off_tw1, 1 << p->log2r, false, s);
@@ -730,6 +746,94 @@ int fft2_filter_ifft2_backward(gbfft_plan_t p, const float *img, const float *H,
     }
     return launch(p, GBFFT_STAGE_COLS_GRAD, s, [&] {
         return launch_grad_scatter(grad_T, grad_T + (size_t)(cols / 2) * rows, grad_H, rows, cols, s);
+    });
+}
+
+int fft2_slab_plan_create(int64_t rows, int64_t cols, int nranks, int rank, gbfft_plan_t *out) {
+    if (!out) return GBFFT_ERR_NULL;
+    *out = nullptr;
+    const int lr = ilog2_exact(rows), lc = ilog2_exact(cols), ln = ilog2_exact(nranks);
+    if (lr < 1 || lc < 2 || lr > kMax2DLog2 || lc > kMax2DLog2 || ln < 0) return GBFFT_ERR_INVALID_SIZE;
+    if (rank < 0 || rank >= nranks) return GBFFT_ERR_INVALID_VALUE;
+    // every rank: whole row-pass blocks of pairs and at least one column
+    int g = rows_pairs_per_block((int)cols);
+    if (g > rows / 2) g = (int)(rows / 2);
+    const int64_t pairs = rows / 2 / nranks;
+    if (pairs < g || pairs % g != 0 || cols / 2 / nranks < 1) return GBFFT_ERR_INVALID_SIZE;
+    gbfft_plan *p = new (std::nothrow) gbfft_plan();
+    if (!p) return GBFFT_ERR_UNSUPPORTED;
+    p->kind = KIND_SLAB;
+    p->dtype = GBFFT_C64;
+    p->batch = 1;
+    p->log2r = lr;
+    p->log2c = lc;
+    p->nranks = nranks;
+    p->rank = rank;
+    layout(p);
+    *out = p;
+    return GBFFT_OK;
+}
+
+int fft2_slab_exchange_elems(gbfft_plan_t p, int64_t *count) {
+    if (!p || !count) return GBFFT_ERR_NULL;
+    if (p->kind != KIND_SLAB) return GBFFT_ERR_INVALID_VALUE;
+    *count = ((int64_t(1) << p->log2c) / 2) * ((int64_t(1) << p->log2r) / p->nranks);
+    return GBFFT_OK;
+}
+
+static int slab_ready(gbfft_plan *p) {
+    int rc = check_plan_ready(p);
+    if (rc) return rc;
+    return p->kind == KIND_SLAB ? GBFFT_OK : GBFFT_ERR_INVALID_VALUE;
+}
+
+int fft2_slab_rows_forward(gbfft_plan_t p, const float *img, void *send, gbfft_stream_t stream) {
+    int rc = slab_ready(p);
+    if (rc) return rc;
+    if (!img || !send) return GBFFT_ERR_NULL;
+    if (misaligned(img) || misaligned(send)) return GBFFT_ERR_MISALIGNED;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int rows = 1 << p->log2r, cols = 1 << p->log2c;
+    const int ld = rows / p->nranks;  // this rank's slots per column
+    return launch(p, GBFFT_STAGE_ROWS_FWD, s, [&] {
+        return launch_rows_fwd(img, send, rows, cols, 1, p->ws + p->off_tw0, s, Slab{p->rank * ld / 2, ld});
+    });
+}
+
+int fft2_slab_columns(gbfft_plan_t p, void *recv, const float *H, gbfft_stream_t stream) {
+    int rc = slab_ready(p);
+    if (rc) return rc;
+    if (!recv || !H) return GBFFT_ERR_NULL;
+    if (misaligned(recv) || misaligned(H)) return GBFFT_ERR_MISALIGNED;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int rows = 1 << p->log2r, cols = 1 << p->log2c;
+    const int mloc = cols / 2 / p->nranks, kbase = p->rank * mloc;
+    const int ld = rows / p->nranks;
+    float *hs = reinterpret_cast<float *>(p->ws + p->off_hs);
+    float *beta = reinterpret_cast<float *>(p->ws + p->off_beta);
+    const float scale = (float)(1.0 / ((double)rows * cols));
+    rc = launch(p, GBFFT_STAGE_FILTER_PREP, s, [&] {
+        return launch_filter_prep(H, hs, beta, rows, cols, 1, scale, 0, 0, 0, s, kbase, mloc);
+    });
+    if (rc) return rc;
+    return launch(p, GBFFT_STAGE_COLS, s, [&] {
+        return launch_cols_filter(recv, hs, beta, 0, 0, rows, cols, 1, p->ws + p->off_tw1,
+                                  reinterpret_cast<int *>(p->ws + p->off_status), s,
+                                  ColSlab{ilog2_exact(ld), mloc, kbase});
+    });
+}
+
+int fft2_slab_rows_inverse(gbfft_plan_t p, const void *back, float *out, gbfft_stream_t stream) {
+    int rc = slab_ready(p);
+    if (rc) return rc;
+    if (!back || !out) return GBFFT_ERR_NULL;
+    if (misaligned(back) || misaligned(out)) return GBFFT_ERR_MISALIGNED;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int rows = 1 << p->log2r, cols = 1 << p->log2c;
+    const int ld = rows / p->nranks;
+    return launch(p, GBFFT_STAGE_ROWS_INV, s, [&] {
+        return launch_rows_inv(back, out, rows, cols, 1, p->ws + p->off_tw0,
+                               reinterpret_cast<int *>(p->ws + p->off_status), s, Slab{p->rank * ld / 2, ld});
     });
 }
 

@@ -11,11 +11,11 @@ namespace gbfft {
 template <int N>
 __global__ void __launch_bounds__(ColCfg<N>::THREADS, 2)
     k_cols_filter(float2 *spec, const float *__restrict__ hs, const float *__restrict__ beta, long long hs_img,
-                  long long beta_img, int M, int log2g, const float2 *__restrict__ tw) {
+                  long long beta_img, int M, int log2g, const float2 *__restrict__ tw, ColSlab cs) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const size_t y = blockIdx.y;
     cols_body<N>(spec + y * (M / 2) * N, PreparedFilter{hs + y * hs_img, beta + y * beta_img, N}, M, log2g, tw,
-                 blockIdx.x, smraw);
+                 blockIdx.x, smraw, Fp32Fft(), cs);
 }
 
 // The column pass with an analytic filter (cols_impl.cuh) computed in place.
@@ -105,7 +105,7 @@ cudaError_t launch_cols_spectrum(const void *spec, float *mag_T, float *nyq, flo
 // ---- The column pass through the TMA (columns of 4096 rows: 256 threads per
 // column, one column per block at a time; taller columns use the
 // one-column-per-block kernel).  A column's N slots (contiguous, slot order) are viewed
-// as N/16 rows of 128 bytes and move as one 2D tensor box with the 128-byte
+// as N/16 rows of 128 bytes and move as 2D tensor boxes with the 128-byte
 // swizzle (the 16-byte chunk c of row r sits at chunk c ^ (r mod 8)), which
 // keeps the threads' slot-order reads and writes free of bank conflicts; the
 // prepared filter column arrives by a bulk copy.  Each block is persistent:
@@ -114,11 +114,15 @@ cudaError_t launch_cols_spectrum(const void *spec, float *mag_T, float *nyq, flo
 // bounded waits as in fourstep.cu).  Results go back into the buffer in the
 // swizzled slot layout and leave by tensor stores; before a buffer is
 // reloaded, its stores must have read it.  The arithmetic is cols_body's.
+// A column of a decomposed image (layout.cuh, ColSlab) arrives in `nchunk`
+// runs of `crows` rows, run q at row q * cstride + c * crows (one image); the
+// runs land back to back in the buffer, so the slot order in shared memory is
+// the same.  One image: nchunk = 1, crows = N/16.
 template <int N> struct ColTmaCfg {
     typedef ColCfg<N> C;
     static constexpr int E = C::E, T = C::T, THREADS = C::THREADS;
     static_assert(C::W == 1 && T >= 64, "one column per block, slot rows aligned to the swizzle");
-    static constexpr int ROWS = N / 16, BOXR = ROWS < 256 ? ROWS : 256;
+    static constexpr int ROWS = N / 16;
     static constexpr size_t BUF = ((size_t)padded_len(N) * sizeof(float2) + 1023) / 1024 * 1024;
     static constexpr size_t FB = (size_t)N * sizeof(float);
     static constexpr size_t SMEM = 1024 + 2 * BUF + 2 * FB + 32;  // alignment slack, buffers, 2 mbarriers
@@ -138,7 +142,8 @@ template <int N>
 __device__ __noinline__ void cols_tma_column(const CUtensorMap *map, float2 *bf, const float *h,
                                              const float *bt, long long c, bool col0, bool prefetch, int b,
                                              const float2 *__restrict__ tw, int log2g, unsigned char *base,
-                                             const float *hs, long long hs_img, int log2half) {
+                                             const float *hs, long long hs_img, int log2half, int crows,
+                                             int boxr, long long cstride, int nchunk) {
     typedef ColTmaCfg<N> K;
     constexpr int E = K::E, T = K::T;
     const int t = threadIdx.x;
@@ -161,7 +166,9 @@ __device__ __noinline__ void cols_tma_column(const CUtensorMap *map, float2 *bf,
         uint64_t *bar = reinterpret_cast<uint64_t *>(base + 2 * K::BUF + 2 * K::FB) + (b ^ 1);
         bulk_wait_read();  // the other buffer's stores have read it
         mbar_expect_tx(bar, (uint32_t)(N * sizeof(float2) + N * sizeof(float)));
-        for (int r = 0; r < K::ROWS; r += K::BOXR) tma_load_2d(nb + r * 16, map, 0, (int)(cn * K::ROWS + r), bar);
+        for (int q = 0; q < nchunk; ++q)
+            for (int r = 0; r < crows; r += boxr)
+                tma_load_2d(nb + (q * crows + r) * 16, map, 0, (int)(q * cstride + cn * crows + r), bar);
         bulk_load(nf, hs + (cn >> log2half) * hs_img + (cn & ((1LL << log2half) - 1)) * N, N * sizeof(float), bar);
     }
     // the first exchange starts with a block barrier: every thread has read
@@ -190,7 +197,9 @@ __device__ __noinline__ void cols_tma_column(const CUtensorMap *map, float2 *bf,
     fence_async_smem();
     __syncthreads();
     if (t == 0) {
-        for (int r = 0; r < K::ROWS; r += K::BOXR) tma_store_2d(map, 0, (int)(c * K::ROWS + r), bf + r * 16);
+        for (int q = 0; q < nchunk; ++q)
+            for (int r = 0; r < crows; r += boxr)
+                tma_store_2d(map, 0, (int)(q * cstride + c * crows + r), bf + (q * crows + r) * 16);
         bulk_commit();
     }
 }
@@ -199,7 +208,8 @@ template <int N>
 __global__ void __launch_bounds__(ColCfg<N>::THREADS, 2)
     k_cols_filter_tma(const __grid_constant__ CUtensorMap map, const float *__restrict__ hs,
                       const float *__restrict__ beta, long long hs_img, long long beta_img, int log2half,
-                      long long ncols, int log2g, const float2 *__restrict__ tw, int *status) {
+                      long long ncols, int log2g, const float2 *__restrict__ tw, int *status, int crows, int boxr,
+                      long long cstride, int nchunk, int kbase) {
     typedef ColTmaCfg<N> K;
     extern __shared__ __align__(1024) unsigned char smraw[];
     unsigned char *base = smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u);  // the swizzle repeats every 1 KB
@@ -215,7 +225,9 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, 2)
     if (t == 0 && c < ncols) {  // the first column and its filter into buffer 0
         mbar_expect_tx(&bar[0], (uint32_t)(N * sizeof(float2) + N * sizeof(float)));
         float2 *b0 = reinterpret_cast<float2 *>(base);
-        for (int r = 0; r < K::ROWS; r += K::BOXR) tma_load_2d(b0 + r * 16, &map, 0, (int)(c * K::ROWS + r), &bar[0]);
+        for (int q = 0; q < nchunk; ++q)
+            for (int r = 0; r < crows; r += boxr)
+                tma_load_2d(b0 + (q * crows + r) * 16, &map, 0, (int)(q * cstride + c * crows + r), &bar[0]);
         bulk_load(base + 2 * K::BUF, hs + (c >> log2half) * hs_img + (c & hmask) * N, N * sizeof(float), &bar[0]);
     }
     for (int it = 0; c < ncols; c += gridDim.x, ++it) {
@@ -230,8 +242,9 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, 2)
         }
         cols_tma_column<N>(&map, reinterpret_cast<float2 *>(base + b * K::BUF),
                            reinterpret_cast<const float *>(base + 2 * K::BUF + b * K::FB),
-                           beta + (c >> log2half) * beta_img, c, (c & hmask) == 0, c + gridDim.x < ncols, b, tw,
-                           log2g, base, hs, hs_img, log2half);
+                           beta + (c >> log2half) * beta_img, c, kbase == 0 && (c & hmask) == 0,
+                           c + gridDim.x < ncols, b, tw, log2g, base, hs, hs_img, log2half, crows, boxr, cstride,
+                           nchunk);
     }
     if (t == 0) bulk_wait_read();  // every store has read its buffer before the block's memory goes
 }
@@ -239,17 +252,24 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, 2)
 template <int N>
 static cudaError_t run_cols_tma(void *spec, const float *hs, const float *beta, long long hs_img, long long beta_img,
                                 int cols, int nimg, int log2g, const void *tw, int *status, cudaStream_t s,
-                                bool *used) {
+                                bool *used, ColSlab cs) {
     typedef ColTmaCfg<N> K;
     *used = false;
     const EncodeTiledFn enc = encode_tiled();
     if (!enc || !status || hs_img % 4 != 0) return cudaSuccess;
-    const long long ncols = (long long)(cols / 2) * nimg;
+    const long long ncols = cs.ls ? cs.mloc : (long long)(cols / 2) * nimg;
+    // runs of a column: one of N/16 rows, or one per rank of 2^ls / 16 rows
+    // each (whole 1 KB swizzle periods, so every run lands 1024-byte aligned)
+    const int crows = cs.ls ? (1 << cs.ls) / 16 : K::ROWS;
+    const int nchunk = cs.ls ? N >> cs.ls : 1;
+    if (crows < 8 || crows % 8 != 0) return cudaSuccess;
+    const int boxr = crows < 256 ? crows : 256;
+    const long long cstride = cs.ls ? (long long)cs.mloc * crows : 0;
     if (ncols * K::ROWS > 0x7fffffffLL) return cudaSuccess;
     // the spectra as rows of 16 slots (128 bytes): {32 floats, ncols * N / 16 rows}
     cuuint64_t dims[2] = {32, (cuuint64_t)(ncols * K::ROWS)};
     cuuint64_t strides[1] = {128};
-    cuuint32_t box[2] = {32, (cuuint32_t)K::BOXR};
+    cuuint32_t box[2] = {32, (cuuint32_t)boxr};
     cuuint32_t estr[2] = {1, 1};
     CUtensorMap map;
     if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, spec, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -270,30 +290,33 @@ static cudaError_t run_cols_tma(void *spec, const float *hs, const float *beta, 
     }
     const long long rounds = (ncols + slots - 1) / slots;
     const long long grid = (ncols + rounds - 1) / rounds;  // the fewest blocks for the same number of rounds
-    kern<<<(unsigned)grid, K::THREADS, K::SMEM, s>>>(map, hs, beta, hs_img, beta_img, ilog2(cols / 2), ncols, log2g,
-                                                     static_cast<const float2 *>(tw), status);
+    const int log2half = cs.ls ? ilog2(cs.mloc) : ilog2(cols / 2);
+    kern<<<(unsigned)grid, K::THREADS, K::SMEM, s>>>(map, hs, beta, hs_img, beta_img, log2half, ncols, log2g,
+                                                     static_cast<const float2 *>(tw), status, crows, boxr, cstride,
+                                                     nchunk, cs.kbase);
     *used = true;
     return cudaGetLastError();
 }
 
 template <int N>
 static cudaError_t run_cols(void *spec, const float *hs, const float *beta, long long hs_img, long long beta_img,
-                            int cols, int nimg, int log2g, const void *tw, int *status, cudaStream_t s) {
+                            int cols, int nimg, int log2g, const void *tw, int *status, cudaStream_t s, ColSlab cs) {
     typedef ColCfg<N> K;
     if constexpr (N >= 4096 && K::W == 1 && K::THREADS == 256) {
         if ((1 << log2g) <= K::T && cols >= 4) {
             bool used = false;
-            cudaError_t e = run_cols_tma<N>(spec, hs, beta, hs_img, beta_img, cols, nimg, log2g, tw, status, s, &used);
+            cudaError_t e =
+                run_cols_tma<N>(spec, hs, beta, hs_img, beta_img, cols, nimg, log2g, tw, status, s, &used, cs);
             if (e != cudaSuccess || used) return e;
         }
     }
     auto kern = k_cols_filter<N>;
     cudaError_t e = set_smem_attrs((const void *)kern, K::SMEM, 2);
     if (e != cudaSuccess) return e;
-    const int half = cols / 2;
+    const int half = cs.ls ? cs.mloc : cols / 2;
     dim3 grid((half + K::W - 1) / K::W, nimg);
     kern<<<grid, K::THREADS, K::SMEM, s>>>(static_cast<float2 *>(spec), hs, beta, hs_img, beta_img, cols, log2g,
-                                           static_cast<const float2 *>(tw));
+                                           static_cast<const float2 *>(tw), cs);
     return cudaGetLastError();
 }
 
@@ -344,13 +367,14 @@ cudaError_t launch_cols_analytic(void *spec, int kind, double p0, double p1, int
 }
 
 cudaError_t launch_cols_filter(void *spec, const float *hs, const float *beta, long long hs_img, long long beta_img,
-                               int rows, int cols, int nimg, const void *tw_rows, int *status, cudaStream_t s) {
+                               int rows, int cols, int nimg, const void *tw_rows, int *status, cudaStream_t s,
+                               ColSlab cs) {
     int g = rows_pairs_per_block(cols);
     if (g > rows / 2) g = rows / 2;
     const int log2g = ilog2(g);
     switch (ilog2(rows)) {
 #define GBFFT_CASE(L) \
-    case L: return run_cols<(1 << L)>(spec, hs, beta, hs_img, beta_img, cols, nimg, log2g, tw_rows, status, s);
+    case L: return run_cols<(1 << L)>(spec, hs, beta, hs_img, beta_img, cols, nimg, log2g, tw_rows, status, s, cs);
         GBFFT_CASE(1) GBFFT_CASE(2) GBFFT_CASE(3) GBFFT_CASE(4) GBFFT_CASE(5) GBFFT_CASE(6) GBFFT_CASE(7)
         GBFFT_CASE(8) GBFFT_CASE(9) GBFFT_CASE(10) GBFFT_CASE(11) GBFFT_CASE(12) GBFFT_CASE(13)
 #undef GBFFT_CASE

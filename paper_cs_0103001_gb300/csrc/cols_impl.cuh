@@ -102,23 +102,35 @@ struct AnalyticFilter {
     __device__ __forceinline__ float b(int u) const { return 0.5f * s * (H(u, 0) - H(u, M >> 1)); }
 };
 
+// With cs.ls > 0 the block works on the column block of a decomposed image
+// (layout.cuh, ColSlab): local columns 0 .. cs.mloc - 1 (global kbase + kl),
+// slot s of column kl at spec + ((s >> ls) mloc + kl) 2^ls + (s mod 2^ls); the
+// prepared filter holds those columns only (filt.h(u, kl)).
 template <int N, typename FFT = Fp32Fft, typename FILT = PreparedFilter>
 __device__ __forceinline__ void cols_body(float2 *spec, FILT filt, int M, int log2g, const float2 *__restrict__ tw,
-                                          int bx, unsigned char *smraw, FFT fft = FFT()) {
+                                          int bx, unsigned char *smraw, FFT fft = FFT(),
+                                          ColSlab cs = ColSlab{0, 0, 0}) {
     typedef ColCfg<N> K;
     constexpr int E = K::E, T = K::T, W = K::W;
     const int w = threadIdx.x / T;
     const int t = threadIdx.x - w * T;
     float2 *ex = reinterpret_cast<float2 *>(smraw) + w * padded_len(N);
-    const int half = M >> 1;
+    const int half = cs.ls ? cs.mloc : M >> 1;  // columns of this launch
     const int k0 = bx * W + w;
     const bool active = k0 < half;  // narrow spectra: surplus column groups idle
     const int k = active ? k0 : 0;
+    const bool has0 = cs.kbase == 0 && bx == 0;  // the block holds global column 0
+    const bool kz = cs.kbase + k == 0;            // this group's column is global column 0
     float2 *col = spec + (size_t)k * N;
+    auto at = [&](int s) -> float2 * {
+        if (cs.ls == 0) return col + s;
+        const int msk = (1 << cs.ls) - 1;
+        return spec + ((size_t)((s >> cs.ls) * cs.mloc + k) << cs.ls) + (s & msk);
+    };
 
     float2 v[E];
 #pragma unroll
-    for (int e = 0; e < E; ++e) v[e] = active ? col[slot_e<N, E, T>(t, e, log2g)] : make_float2(0.f, 0.f);
+    for (int e = 0; e < E; ++e) v[e] = active ? *at(slot_e<N, E, T>(t, e, log2g)) : make_float2(0.f, 0.f);
 
     float h[E];
     if constexpr (FILT::EARLY) {
@@ -133,13 +145,13 @@ __device__ __forceinline__ void cols_body(float2 *spec, FILT filt, int M, int lo
         for (int e = 0; e < E; ++e) h[e] = filt.h(t + T * e, k);
     }
 
-    if (bx == 0) {  // the group of column 0 needs Q[-u] (uniform per block)
+    if (has0) {  // the group of column 0 needs Q[-u] (uniform per block)
         __syncthreads();
 #pragma unroll
         for (int e = 0; e < E; ++e) ex[pad16(t + T * e)] = v[e];
         __syncthreads();
     }
-    if (k != 0) {
+    if (!kz) {
 #pragma unroll
         for (int e = 0; e < E; ++e) v[e] = cscale(v[e], h[e]);
     } else {
@@ -156,7 +168,7 @@ __device__ __forceinline__ void cols_body(float2 *spec, FILT filt, int M, int lo
 
     if (active) {
 #pragma unroll
-        for (int e = 0; e < E; ++e) col[slot_e<N, E, T>(t, e, log2g)] = v[e];
+        for (int e = 0; e < E; ++e) *at(slot_e<N, E, T>(t, e, log2g)) = v[e];
     }
 }
 

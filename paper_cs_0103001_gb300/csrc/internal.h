@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "layout.cuh"
+
 namespace gbfft {
 
 // Largest length the one-pass batched kernel handles (whole transform in one
@@ -74,22 +76,30 @@ cudaError_t launch_cols_spectrum(const void *spec, float *mag_T, float *nyq, flo
                                  const void *tw_rows, cudaStream_t s);
 // Forward row pass: nimg real images [rows][cols] -> half spectra
 // [nimg][cols/2][rows] complex64, slot order (layout.cuh).
+// With a slab (one image): only pairs slab.p0 .., into [cols/2][slab.ld].
 cudaError_t launch_rows_fwd(const float *img, void *spec, int rows, int cols, int nimg, const void *tw_cols,
-                            cudaStream_t s);
+                            cudaStream_t s, Slab slab = Slab{0, 0});
 // Prepared filter (rows_impl.cuh) for nimg filters H + i * h_stride into
-// hs + i * hs_img, beta + i * beta_img.
+// hs + i * hs_img, beta + i * beta_img.  kcnt > 0: only the half-spectrum
+// columns kbeg .. kbeg + kcnt - 1, written as hs columns 0 .. kcnt - 1 (beta
+// only when the range holds column 0).
 cudaError_t launch_filter_prep(const float *H, float *hs, float *beta, int rows, int cols, int nimg, float scale,
-                               long long h_stride, long long hs_img, long long beta_img, cudaStream_t s);
+                               long long h_stride, long long hs_img, long long beta_img, cudaStream_t s,
+                               int kbeg = 0, int kcnt = 0);
 // Column pass with an analytic filter computed in the kernel (no filter
 // array): kind 1 Gaussian (p0 = sigma in bins), 2 Butterworth (p0 = order,
 // p1 = cutoff D0 in bins), 3 disc of Eq. filtro (p0 = radius b); cols_impl.cuh.
 cudaError_t launch_cols_analytic(void *spec, int kind, double p0, double p1, int rows, int cols, int nimg,
                                  const void *tw_rows, cudaStream_t s);
 // hs_img / beta_img: elements between images' prepared filters (0 = shared)
+// With cs.ls > 0 (one image): the column block of a decomposed image, spec in
+// the received layout [ranks][cs.mloc][2^cs.ls] (layout.cuh, ColSlab), hs the
+// prepared filter of those columns only.
 cudaError_t launch_cols_filter(void *spec, const float *hs, const float *beta, long long hs_img, long long beta_img,
-                               int rows, int cols, int nimg, const void *tw_rows, int *status, cudaStream_t s);
+                               int rows, int cols, int nimg, const void *tw_rows, int *status, cudaStream_t s,
+                               ColSlab cs = ColSlab{0, 0, 0});
 cudaError_t launch_rows_inv(const void *spec, float *out, int rows, int cols, int nimg, const void *tw_cols,
-                            int *status, cudaStream_t s);
+                            int *status, cudaStream_t s, Slab slab = Slab{0, 0});
 // Tensor-core variants (tc2d.cu): radix-16 passes as split-BF16 DFT-matrix
 // products with `terms` = 2 or 3 BF16 parts per operand; sides 512..4096.
 bool tc_supported(int rows, int cols);

@@ -20,6 +20,25 @@
 
 namespace gbfft {
 
+// Row-slab share of an image decomposed over ranks (Sec. 2's division of the
+// work among processes, here by rows): a rank owns the pairs p0 .. p0 + P - 1
+// (p0 and P multiples of the row pass's pairs per block), i.e. 2P slots of
+// every half-spectrum column, which it keeps as [M/2][ld] with ld = 2P
+// (column stride ld instead of N).  Global slot s of column k then lives on
+// rank s / ld at local slot s mod ld.  The default {0, 0} is the whole image.
+struct Slab {
+    int p0, ld;
+};
+
+// Column-block share of the same decomposition: a rank transforms the Mloc
+// half-spectrum columns kbase .. kbase + Mloc - 1, received from the ranks as
+// [ranks][Mloc][ld] (chunk q = rank q's slots of these columns).  Local column
+// kl, global slot s then sits at ((s / ld) Mloc + kl) ld + s mod ld, ld = 2^ls.
+// ls = 0 means one contiguous column per k ([M/2][N], the whole image).
+struct ColSlab {
+    int ls, mloc, kbase;
+};
+
 // pair index and side (0: first row, 1: mirror row) of row x of an N-row image
 __host__ __device__ __forceinline__ void pair_of(int x, int N, int &p, int &side) {
     const int h = N >> 1;

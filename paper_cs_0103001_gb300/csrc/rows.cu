@@ -21,19 +21,21 @@ int rows_pairs_per_block(int cols) {
 template <int M>
 __global__ void __launch_bounds__(RowCfg<M>::THREADS, RowCfg<M>::THREADS <= 512 ? 2 : 1)
     k_rows_fwd(const float *__restrict__ img, float2 *__restrict__ spec, int N, int log2g,
-               const float2 *__restrict__ tw) {
+               const float2 *__restrict__ tw, Slab slab) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const size_t y = blockIdx.y;
-    rows_fwd_body<M>(img + y * N * M, spec + y * (M / 2) * N, N, log2g, tw, blockIdx.x, smraw);
+    rows_fwd_body<M>(img + y * N * M, spec + y * (M / 2) * N, N, log2g, tw, blockIdx.x, smraw, Fp32Fft(),
+                     Crop{0, 0}, nullptr, 0, slab);
 }
 
 template <int M>
 __global__ void __launch_bounds__(RowCfg<M>::THREADS, RowCfg<M>::THREADS <= 512 ? 2 : 1)
     k_rows_inv(const float2 *__restrict__ spec, float *__restrict__ out, int N, int log2g,
-               const float2 *__restrict__ tw) {
+               const float2 *__restrict__ tw, Slab slab) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const size_t y = blockIdx.y;
-    rows_inv_body<M>(spec + y * (M / 2) * N, out + y * N * M, N, log2g, tw, blockIdx.x, smraw);
+    rows_inv_body<M>(spec + y * (M / 2) * N, out + y * N * M, N, log2g, tw, blockIdx.x, smraw, Fp32Fft(),
+                     Crop{0, 0}, nullptr, 0, nullptr, nullptr, slab);
 }
 
 // Row passes of a zero-padded image (Sec. 5 application path): image y of the
@@ -69,20 +71,22 @@ __global__ void __launch_bounds__(RowCfg<M>::THREADS, RowCfg<M>::THREADS <= 512 
 template <int R, bool QUADS>
 __global__ void __launch_bounds__(256)
     k_filter_prep(const float *__restrict__ H, float *__restrict__ hs, float *__restrict__ beta, int N, int M,
-                  int log2k, float scale, long long h_stride, long long hs_img, long long beta_img) {
+                  int log2k, float scale, long long h_stride, long long hs_img, long long beta_img, int kbeg) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const size_t z = blockIdx.z;
     filter_prep_tile<R, QUADS>(H + z * h_stride, hs + z * hs_img, beta + z * beta_img, N, M, log2k, scale,
-                               blockIdx.x * R, blockIdx.y << log2k, reinterpret_cast<float *>(smraw));
+                               blockIdx.x * R, kbeg + (blockIdx.y << log2k), reinterpret_cast<float *>(smraw), kbeg);
 }
 
 cudaError_t launch_filter_prep(const float *H, float *hs, float *beta, int rows, int cols, int nimg, float scale,
-                               long long h_stride, long long hs_img, long long beta_img, cudaStream_t s) {
-    const int kk = cols / 2 < kPrepCols ? cols / 2 : kPrepCols;
+                               long long h_stride, long long hs_img, long long beta_img, cudaStream_t s, int kbeg,
+                               int kcnt) {
+    const int ncol = kcnt > 0 ? kcnt : cols / 2;  // half-spectrum columns to prepare
+    const int kk = ncol < kPrepCols ? ncol : kPrepCols;
     const int rr = rows < kPrepRows ? rows : kPrepRows;  // rows per tile
     const bool quads = kk >= 4 && rr >= 4;  // four columns per load, four rows per store
     const size_t smem = (size_t)kk * (rr + 1) * sizeof(float);
-    dim3 grid(rows / rr, (cols / 2) / kk, nimg);
+    dim3 grid(rows / rr, ncol / kk, nimg);
     cudaError_t e = cudaErrorInvalidValue;
     switch (rr * 2 + (quads ? 1 : 0)) {
 #define GBFFT_R(RR, Q)                                                                                         \
@@ -90,7 +94,7 @@ cudaError_t launch_filter_prep(const float *H, float *hs, float *beta, int rows,
         e = set_smem_attrs((const void *)k_filter_prep<RR, Q>, smem);                                          \
         if (e != cudaSuccess) return e;                                                                        \
         k_filter_prep<RR, Q><<<grid, 256, smem, s>>>(H, hs, beta, rows, cols, ilog2(kk), scale, h_stride, hs_img, \
-                                                     beta_img);                                                \
+                                                     beta_img, kbeg);                                          \
         return cudaGetLastError();
         GBFFT_R(2, false) GBFFT_R(4, false) GBFFT_R(8, false) GBFFT_R(16, false) GBFFT_R(32, false)
         GBFFT_R(4, true) GBFFT_R(8, true) GBFFT_R(16, true) GBFFT_R(32, true)
@@ -114,12 +118,12 @@ static int log2_pairs_per_block(int rows, int cols) {
 template <int M>
 __global__ void __launch_bounds__(RowCfg<M>::THREADS, RowCfg<M>::THREADS <= 512 ? 2 : 1)
     k_rows_fwd_tma(const float *__restrict__ img, float2 *__restrict__ spec, int N, int log2g,
-                   const float2 *__restrict__ tw, const __grid_constant__ CUtensorMap omap) {
+                   const float2 *__restrict__ tw, const __grid_constant__ CUtensorMap omap, Slab slab) {
     extern __shared__ __align__(1024) unsigned char smraw[];
     unsigned char *base = smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u);  // the box's swizzle period
     const size_t y = blockIdx.y;
     rows_fwd_body<M, Fp32Fft, false, true>(img + y * N * M, spec + y * (M / 2) * N, N, log2g, tw, blockIdx.x, base,
-                                           Fp32Fft(), Crop{0, 0}, &omap, (int)y);
+                                           Fp32Fft(), Crop{0, 0}, &omap, (int)y, slab);
 }
 
 // Tensor map of the half spectra of nimg images ({2 rows floats, cols/2
@@ -138,28 +142,32 @@ static bool spec_map(CUtensorMap *map, void *spec, int rows, int cols, int nimg,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+// slab.ld > 0: one image, pairs slab.p0 .. slab.p0 + slab.ld / 2 - 1 into
+// [M/2][slab.ld] (the launcher's caller checks that they fill whole blocks)
 template <int M>
-static cudaError_t run_rows_fwd(const float *img, void *spec, int rows, int nimg, const void *tw, cudaStream_t s) {
+static cudaError_t run_rows_fwd(const float *img, void *spec, int rows, int nimg, const void *tw, cudaStream_t s,
+                                Slab slab) {
     typedef RowCfg<M> K;
+    const int ld = slab.ld ? slab.ld : rows;  // column stride of the half spectra written
     if constexpr (M >= 256 && 4 * K::PPC <= 256 && K::THREADS <= 512) {
         const int lg = log2_pairs_per_block(rows, M);
         CUtensorMap map;
-        if ((1 << lg) == K::PPC && spec_map(&map, spec, rows, M, nimg, K::PPC)) {
+        if ((1 << lg) == K::PPC && spec_map(&map, spec, ld, M, nimg, K::PPC)) {
             const size_t smem = K::SMEM_FWD + 1024;
             cudaError_t e = set_smem<M>((const void *)k_rows_fwd_tma<M>, smem);
             if (e != cudaSuccess) return e;
-            dim3 grid((rows / 2) >> lg, nimg);
+            dim3 grid((ld / 2) >> lg, nimg);
             k_rows_fwd_tma<M><<<grid, K::THREADS, smem, s>>>(img, static_cast<float2 *>(spec), rows, lg,
-                                                             static_cast<const float2 *>(tw), map);
+                                                             static_cast<const float2 *>(tw), map, slab);
             return cudaGetLastError();
         }
     }
     cudaError_t e = set_smem<M>((const void *)k_rows_fwd<M>, K::SMEM_FWD);
     if (e != cudaSuccess) return e;
     const int lg = log2_pairs_per_block(rows, M);
-    dim3 grid((rows / 2) >> lg, nimg);
+    dim3 grid((ld / 2) >> lg, nimg);
     k_rows_fwd<M><<<grid, K::THREADS, K::SMEM_FWD, s>>>(img, static_cast<float2 *>(spec), rows, lg,
-                                                    static_cast<const float2 *>(tw));
+                                                    static_cast<const float2 *>(tw), slab);
     return cudaGetLastError();
 }
 
@@ -168,38 +176,40 @@ static cudaError_t run_rows_fwd(const float *img, void *spec, int rows, int nimg
 template <int M>
 __global__ void __launch_bounds__(RowCfg<M>::THREADS, 2)
     k_rows_inv_tma(float *__restrict__ out, int N, int log2g, const float2 *__restrict__ tw,
-                   const __grid_constant__ CUtensorMap imap, int *status) {
+                   const __grid_constant__ CUtensorMap imap, int *status, Slab slab) {
     extern __shared__ __align__(1024) unsigned char smraw[];
     unsigned char *base = smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u);  // the box's swizzle period
     uint64_t *bar = reinterpret_cast<uint64_t *>(base + RowCfg<M>::SMEM);
     const size_t y = blockIdx.y;
     rows_inv_body<M, Fp32Fft, false, true>(nullptr, out + y * N * M, N, log2g, tw, blockIdx.x, base, Fp32Fft(),
-                                           Crop{0, 0}, &imap, (int)y, bar, status);
+                                           Crop{0, 0}, &imap, (int)y, bar, status, slab);
 }
 
+// slab.ld > 0: one image, pairs slab.p0 .. from [M/2][slab.ld]
 template <int M>
 static cudaError_t run_rows_inv(const void *spec, float *out, int rows, int nimg, const void *tw, int *status,
-                                cudaStream_t s) {
+                                cudaStream_t s, Slab slab) {
     typedef RowCfg<M> K;
+    const int ld = slab.ld ? slab.ld : rows;  // column stride of the half spectra read
     if constexpr (K::PPC == 2 && K::THREADS <= 512) {
         const int lg = log2_pairs_per_block(rows, M);
         CUtensorMap map;
-        if (status && (1 << lg) == 2 && spec_map(&map, const_cast<void *>(spec), rows, M, nimg, 2)) {
+        if (status && (1 << lg) == 2 && spec_map(&map, const_cast<void *>(spec), ld, M, nimg, 2)) {
             const size_t smem = K::SMEM + 1024 + 16;
             cudaError_t e = set_smem<M>((const void *)k_rows_inv_tma<M>, smem);
             if (e != cudaSuccess) return e;
-            dim3 grid((rows / 2) >> lg, nimg);
+            dim3 grid((ld / 2) >> lg, nimg);
             k_rows_inv_tma<M><<<grid, K::THREADS, smem, s>>>(out, rows, lg, static_cast<const float2 *>(tw), map,
-                                                             status);
+                                                             status, slab);
             return cudaGetLastError();
         }
     }
     cudaError_t e = set_smem<M>((const void *)k_rows_inv<M>, K::SMEM);
     if (e != cudaSuccess) return e;
     const int lg = log2_pairs_per_block(rows, M);
-    dim3 grid((rows / 2) >> lg, nimg);
+    dim3 grid((ld / 2) >> lg, nimg);
     k_rows_inv<M><<<grid, K::THREADS, K::SMEM, s>>>(static_cast<const float2 *>(spec), out, rows, lg,
-                                                    static_cast<const float2 *>(tw));
+                                                    static_cast<const float2 *>(tw), slab);
     return cudaGetLastError();
 }
 
@@ -237,10 +247,10 @@ cudaError_t launch_rows_pad(bool fwd, const void *src, void *dst, int rows, int 
 }
 
 cudaError_t launch_rows_fwd(const float *img, void *spec, int rows, int cols, int nimg, const void *tw_cols,
-                            cudaStream_t s) {
+                            cudaStream_t s, Slab slab) {
     switch (ilog2(cols)) {
 #define GBFFT_CASE(L) \
-    case L: return run_rows_fwd<(1 << L)>(img, spec, rows, nimg, tw_cols, s);
+    case L: return run_rows_fwd<(1 << L)>(img, spec, rows, nimg, tw_cols, s, slab);
         GBFFT_CASE(1) GBFFT_CASE(2) GBFFT_CASE(3) GBFFT_CASE(4) GBFFT_CASE(5) GBFFT_CASE(6) GBFFT_CASE(7)
         GBFFT_CASE(8) GBFFT_CASE(9) GBFFT_CASE(10) GBFFT_CASE(11) GBFFT_CASE(12) GBFFT_CASE(13)
 #undef GBFFT_CASE
@@ -249,10 +259,10 @@ cudaError_t launch_rows_fwd(const float *img, void *spec, int rows, int cols, in
 }
 
 cudaError_t launch_rows_inv(const void *spec, float *out, int rows, int cols, int nimg, const void *tw_cols,
-                            int *status, cudaStream_t s) {
+                            int *status, cudaStream_t s, Slab slab) {
     switch (ilog2(cols)) {
 #define GBFFT_CASE(L) \
-    case L: return run_rows_inv<(1 << L)>(spec, out, rows, nimg, tw_cols, status, s);
+    case L: return run_rows_inv<(1 << L)>(spec, out, rows, nimg, tw_cols, status, s, slab);
         GBFFT_CASE(1) GBFFT_CASE(2) GBFFT_CASE(3) GBFFT_CASE(4) GBFFT_CASE(5) GBFFT_CASE(6) GBFFT_CASE(7)
         GBFFT_CASE(8) GBFFT_CASE(9) GBFFT_CASE(10) GBFFT_CASE(11) GBFFT_CASE(12) GBFFT_CASE(13)
 #undef GBFFT_CASE

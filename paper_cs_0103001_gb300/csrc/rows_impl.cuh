@@ -87,14 +87,15 @@ template <int M, typename FFT = Fp32Fft, bool PAD = false, bool TSTORE = false>
 __device__ __forceinline__ void rows_fwd_body(const float *__restrict__ img, float2 *__restrict__ spec, int N,
                                               int log2g, const float2 *__restrict__ tw, int bx,
                                               unsigned char *smraw, FFT fft = FFT(), Crop crop = Crop{0, 0},
-                                              const CUtensorMap *omap = nullptr, int z = 0) {
+                                              const CUtensorMap *omap = nullptr, int z = 0, Slab slab = Slab{0, 0}) {
     typedef RowCfg<M> K;
     constexpr int E = K::E, T = K::T, H2 = M / 2;
     float2 *sm = reinterpret_cast<float2 *>(smraw);
     const int G = 1 << log2g;
     const int g = threadIdx.x / T;
     const int t = threadIdx.x - g * T;
-    const int p = bx * G + g;
+    const int p = slab.p0 + bx * G + g;
+    const size_t ld = slab.ld ? (size_t)slab.ld : (size_t)N;  // column stride of the half spectra
     const bool active = g < G;  // the grid covers exactly N/2 pairs in groups of G
     int a, b;
     rows_of_pair(active ? p : 0, N, a, b);
@@ -200,12 +201,12 @@ __device__ __forceinline__ void rows_fwd_body(const float *__restrict__ img, flo
             const int g0 = side ? s - G : s;
             const float2 x0 = split_ab<M>(sm + g0 * padded_len(M), k, side);
             const float2 x1 = split_ab<M>(sm + (g0 + 1) * padded_len(M), k, side);
-            *reinterpret_cast<float4 *>(sb + (size_t)k * N + s) = make_float4(x0.x, x0.y, x1.x, x1.y);
+            *reinterpret_cast<float4 *>(sb + k * ld + s) = make_float4(x0.x, x0.y, x1.x, x1.y);
         }
     } else {  // one pair per block (N = 2): its A and B side by side
         for (int k = threadIdx.x; k < H2; k += K::THREADS) {
             const float2 a = split_ab<M>(sm, k, false), b = split_ab<M>(sm, k, true);
-            *reinterpret_cast<float4 *>(sb + (size_t)k * N) = make_float4(a.x, a.y, b.x, b.y);
+            *reinterpret_cast<float4 *>(sb + k * ld) = make_float4(a.x, a.y, b.x, b.y);
         }
     }
 }
@@ -233,14 +234,15 @@ __device__ __forceinline__ void rows_inv_body(const float2 *__restrict__ spec, f
                                               int log2g, const float2 *__restrict__ tw, int bx,
                                               unsigned char *smraw, FFT fft = FFT(), Crop crop = Crop{0, 0},
                                               const CUtensorMap *imap = nullptr, int z = 0, uint64_t *bar = nullptr,
-                                              int *status = nullptr) {
+                                              int *status = nullptr, Slab slab = Slab{0, 0}) {
     typedef RowCfg<M> K;
     constexpr int E = K::E, T = K::T, H2 = M / 2;
     float2 *sm = reinterpret_cast<float2 *>(smraw);
     const int G = 1 << log2g;
     const int g = threadIdx.x / T;
     const int t = threadIdx.x - g * T;
-    const int p = bx * G + g;
+    const int p = slab.p0 + bx * G + g;
+    const size_t ld = slab.ld ? (size_t)slab.ld : (size_t)N;  // column stride of the half spectra
     const bool active = g < G;
     int a, b;
     rows_of_pair(active ? p : 0, N, a, b);
@@ -275,7 +277,7 @@ __device__ __forceinline__ void rows_inv_body(const float2 *__restrict__ spec, f
         const int n = H2 << log2g;
         for (int idx = threadIdx.x; idx < n; idx += K::THREADS) {
             const int k = idx >> log2g, s = (idx & (G - 1)) * 2;
-            const float4 x = *reinterpret_cast<const float4 *>(sb + (size_t)k * N + s);
+            const float4 x = *reinterpret_cast<const float4 *>(sb + k * ld + s);
             stg[stage_pos(k, s, log2g)] = make_float2(x.x, x.y);
             stg[stage_pos(k, s + 1, log2g)] = make_float2(x.z, x.w);
         }
@@ -345,12 +347,13 @@ constexpr int kPrepRows = 32, kPrepCols = 64;  // tile of the preparation
 
 // One tile of the filter preparation (block-wide; blockDim.x threads): rows
 // u0 .. u0 + R - 1, half-spectrum columns k0 .. k0 + K - 1 (K = 2^log2k) of
-// one filter H into hs (row order) and beta; `tile` is K (R + 1) floats of
-// shared memory.  Ends with the tile's global writes (no trailing barrier).
+// one filter H into hs (row order; column k at hs column k - kbeg) and beta;
+// `tile` is K (R + 1) floats of shared memory.  Ends with the tile's global
+// writes (no trailing barrier).
 template <int R, bool QUADS>
 __device__ __forceinline__ void filter_prep_tile(const float *__restrict__ hb, float *__restrict__ hsz,
                                                  float *__restrict__ betaz, int N, int M, int log2k, float scale,
-                                                 int u0, int k0, float *tile) {
+                                                 int u0, int k0, float *tile, int kbeg = 0) {
     constexpr int SR = R + 1;  // tile row stride (odd: conflict-free column writes)
     const int K = 1 << log2k, H2 = M >> 1;
     const float hsc = 0.5f * scale;
@@ -407,13 +410,13 @@ __device__ __forceinline__ void filter_prep_tile(const float *__restrict__ hb, f
         for (int idx = threadIdx.x; idx < m; idx += blockDim.x) {
             const int i = idx / (R / 4), r = (idx % (R / 4)) * 4;
             const float *tr = tile + i * SR + r;
-            *reinterpret_cast<float4 *>(hsb + (size_t)(k0 + i) * N + r) = make_float4(tr[0], tr[1], tr[2], tr[3]);
+            *reinterpret_cast<float4 *>(hsb + (size_t)(k0 - kbeg + i) * N + r) = make_float4(tr[0], tr[1], tr[2], tr[3]);
         }
     } else {
         const int m = K * R;
         for (int idx = threadIdx.x; idx < m; idx += blockDim.x) {
             const int i = idx / R, r = idx % R;
-            hsb[(size_t)(k0 + i) * N + r] = tile[i * SR + r];
+            hsb[(size_t)(k0 - kbeg + i) * N + r] = tile[i * SR + r];
         }
     }
 }

@@ -138,3 +138,23 @@ def test_device_status_checks(nat):
     assert nat.lib.gbfft_selftest_wait_timeout(None, 1, None) == nat.ERR_NULL
     assert nat.lib.gbfft_selftest_wait_timeout(h, 16, None) == nat.ERR_WORKSPACE
     assert nat.lib.fft_plan_destroy(h) == nat.OK
+
+
+def test_slab_plan_validation_without_gpu(nat):
+    h = ctypes.c_void_p()
+    assert nat.lib.fft2_slab_plan_create(4096, 4096, 3, 0, ctypes.byref(h)) == nat.ERR_INVALID_SIZE
+    assert nat.lib.fft2_slab_plan_create(128, 128, 2, 0, ctypes.byref(h)) == nat.ERR_INVALID_SIZE
+    assert nat.lib.fft2_slab_plan_create(4096, 4096, 2, 5, ctypes.byref(h)) == nat.ERR_INVALID_VALUE
+    assert nat.lib.fft2_slab_plan_create(4096, 4096, 2, 1, None) == nat.ERR_NULL
+    assert nat.lib.fft2_slab_plan_create(4096, 4096, 2, 1, ctypes.byref(h)) == nat.OK and h.value
+    n = ctypes.c_int64()
+    assert nat.lib.fft2_slab_exchange_elems(h, ctypes.byref(n)) == nat.OK
+    assert n.value == 2048 * 2048
+    ws = ctypes.c_size_t()
+    assert nat.lib.fft_plan_workspace_bytes(h, ctypes.byref(ws)) == nat.OK and ws.value > 0
+    # no workspace bound yet: every step refuses before touching CUDA
+    buf = ctypes.c_void_p(256)
+    assert nat.lib.fft2_slab_rows_forward(h, buf, buf, None) == nat.ERR_WORKSPACE
+    assert nat.lib.fft2_slab_columns(h, buf, buf, None) == nat.ERR_WORKSPACE
+    assert nat.lib.fft2_slab_rows_inverse(h, buf, buf, None) == nat.ERR_WORKSPACE
+    assert nat.lib.fft_plan_destroy(h) == nat.OK

@@ -81,7 +81,16 @@ def test_autograd_mse_against_finite_differences(gb):
 
 
 def test_backward_differentiable_workload_size(gb):
-    """16 x 2048^2 noisy skies, H = 1: full gradients against the oracle."""
+    """16 x 2048^2 noisy skies, H = 1, the MSE loss against the clean skies:
+    full gradients through torch autograd against the oracle's closed forms.
+
+    Both sides get the same upstream gradient G = dL/dy = 2 (y - clean) / numel
+    at the exact forward, which for H = 1 is the identity (y = noisy), so G
+    is computed on the host from the inputs.  (Taking G from each side's own
+    forward output instead would compare different inputs: y - clean cancels
+    the sky, and the fp32 forward's rounding, within its own tolerance, makes
+    the two G differ by about 4e-6 relative; at bins where the clean sky
+    dominates that alone moves grad_H by about 5e-5.)"""
     import torch
 
     rows = cols = 2048
@@ -89,21 +98,28 @@ def test_backward_differentiable_workload_size(gb):
     clean = np.stack([synth.sky(rows, cols, 5000, 5, b) for b in range(batch)])
     noisy = (clean + synth.real_uniform(clean.shape, 5, 99, low=-30, high=30)).astype(np.float32)
     H = np.ones((rows, cols), np.float32)
+    G = (2.0 * (noisy.astype(np.float64) - clean) / noisy.size).astype(np.float32)
     x = torch.from_numpy(noisy).cuda().requires_grad_(True)
     Ht = torch.from_numpy(H).cuda().requires_grad_(True)
-    loss = torch.mean((gb.fft2_filter_ifft2(x, Ht) - torch.from_numpy(clean).cuda()) ** 2)
-    loss.backward()
-    y = oracle.pipeline(noisy, H)
-    G = 2.0 * (y - clean) / y.size
+    y = gb.fft2_filter_ifft2(x, Ht)
+    torch.sum(y * torch.from_numpy(G).cuda()).backward()  # dL/dy = G exactly
     gi_ref, gh_ref = oracle.pipeline_grad(noisy, H, G)
-    assert max_rel_l2(x.grad.cpu().numpy(), gi_ref, axes=(1, 2)) <= GRAD_TOL
+    err_img = max_rel_l2(x.grad.cpu().numpy(), gi_ref, axes=(1, 2))
+    print(f"grad_img max rel-L2 {err_img:.3e} (bound {GRAD_TOL:.0e})")
+    assert err_img <= GRAD_TOL
     gh = Ht.grad.cpu().numpy().astype(np.float64)
-    # grad_H = s sum_b Re(conj(W G_b) W x_b) multiplies two fp32 spectra whose
-    # errors are bounded normwise by the transform tolerance g = 2e-7 log2(NM)
-    # (||dW x|| <= g ||W x||).  Hence ||d grad_H|| <= 2 g s sum_b ||W G_b|| ||W x_b||
-    # = 2 g sum_b ||G_b|| ||x_b|| (Parseval, s = 1/(NM)).  The relative form of
-    # this bound is large here because the sky's background (100 per pixel)
-    # dominates ||x|| while grad_H lives at the frequencies of the noise.
-    g = 2e-7 * np.log2(rows * cols)
-    bound = 2 * g * sum(np.linalg.norm(G[b]) * np.linalg.norm(noisy[b].astype(np.float64)) for b in range(batch))
-    assert np.linalg.norm(gh - gh_ref) <= bound
+    # every bin but DC to the gradient tolerance
+    mask = np.ones_like(gh, dtype=bool)
+    mask[0, 0] = False
+    err = rel_l2(gh[mask], gh_ref[mask])
+    print(f"grad_H non-DC rel-L2 {err:.3e} (bound {GRAD_TOL:.0e})")
+    assert err <= GRAD_TOL
+    # DC: grad_H[0,0] = s sum_b (sum G_b)(sum x_b).  sum G_b cancels (G is
+    # zero-mean noise), so fp32 can only meet the summation-error bound of a
+    # length-NM sum, log2(NM) eps sum|G_b|, on sum G_b, times s |sum x_b|
+    s = 1.0 / (rows * cols)
+    eps = 2.0 ** -24
+    bound = sum(s * abs(noisy[b].astype(np.float64).sum()) * np.log2(rows * cols) * eps * np.abs(G[b]).sum()
+                for b in range(batch))
+    print(f"grad_H DC error {abs(gh[0, 0] - gh_ref[0, 0]):.3e} (bound {2 * bound:.3e})")
+    assert abs(gh[0, 0] - gh_ref[0, 0]) <= 2 * bound
