@@ -433,6 +433,8 @@ def run_gbfft(args):
                              pipeline4096_analytic_filter=_guard(lambda: variant_analytic(img, flush)),
                              cufft_context=_guard(lambda: variant_cufft_context(img, H, ref, flush)))
             if args.variants else None,
+            "alu_peaks_measured": _guard(lambda: {"fp64_fma_gflops": round(gb.measure_fma_peak(True) / 1e9, 1),
+                                                  "fp32_fma_gflops": round(gb.measure_fma_peak(False) / 1e9, 1)}),
             "clocks": clk,
             "wall_s_timed": round(wall, 4),
         }
@@ -487,15 +489,50 @@ def variant_fft1d(log2n: int, dtype: str = "c64", steps: int = 10, onchip: int =
 
     plan = gb.Plan1D(n, batch, tdt, "cuda", {nat.OPT_ONCHIP: onchip})
     ms = _timed(lambda: plan.forward(x, out=y), steps, 3)
+    ms_inv = _timed(lambda: plan.inverse(x, out=y), steps, 3)
     nbytes = 2 * x.numel() * x.element_size()
-    return {"n": n, "batch": batch, "dtype": dtype, "us": round(ms * 1e3, 1),
-            "gbs_one_pass": round(nbytes / (ms * 1e-3) / 1e9, 1),
-            "gflops_5nlogn": round(5 * n * log2n * batch / (ms * 1e-3) / 1e9, 1)}
+    flops = 5 * n * log2n * batch
+    res = {"n": n, "batch": batch, "dtype": dtype, "us": round(ms * 1e3, 1), "inverse_us": round(ms_inv * 1e3, 1),
+           "gbs_one_pass": round(nbytes / (ms * 1e-3) / 1e9, 1),
+           "gbs_one_pass_inverse": round(nbytes / (ms_inv * 1e-3) / 1e9, 1),
+           "gflops_5nlogn": round(flops / (ms * 1e-3) / 1e9, 1)}
+    if dtype == "c128":
+        # FP64-ALU bound: the nominal 5 N log2 N flops against the measured FP64
+        # FMA rate (2 flops per FMA) of this GPU
+        peak = gb.measure_fma_peak(True)
+        res["roofline"] = {"bound": "alu", "achieved_gflops_5nlogn": res["gflops_5nlogn"],
+                           "peak_gflops_fp64_fma": round(peak / 1e9, 1),
+                           "frac": round(flops / (ms * 1e-3) / peak, 4),
+                           "note": "peak measured by gbfft_measure_fma_peak (independent FP64 FMA chains, all SMs)"}
+    return res
 
 
-def variant_batched(count: int = 512, steps: int = 5):
+def variant_pipeline_tc(precision: int, steps: int = 20):
+    """The headline 4096^2 workload with the radix-16 passes on the tensor
+    cores (GBFFT_OPT_PRECISION 1: two BF16 parts, three products; 2: three
+    parts, six products): median time of flushed steps and rel-L2 to the oracle."""
+    import torch
+
+    import oracle
+    import paper_cs_0103001_gb300 as gb
+    from paper_cs_0103001_gb300 import _native as nat
+
+    img_np, H_np = make_inputs(0)
+    img, H = torch.from_numpy(img_np).cuda(), torch.from_numpy(H_np).cuda()
+    out = torch.empty_like(img)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    plan = gb.Plan2D(ROWS, COLS, 1, "cuda", {nat.OPT_PRECISION: precision})
+    ms = _timed(lambda: plan.filter(img, H, out=out), steps, 3, flush)
+    ref = oracle.pipeline(img_np, H_np)
+    got = out.cpu().numpy().astype(np.float64)
+    return {"precision": precision, "us": round(ms * 1e3, 2),
+            "rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref))}
+
+
+def variant_batched(count: int = 512, steps: int = 5, autotune: bool = True):
     """Uneven batch: `count` skies, sides in {64..2048}, own Gaussian filter
-    each, four persistent launches replayed from a CUDA graph."""
+    each, four persistent launches replayed from a CUDA graph (blocks per SM
+    tuned first unless autotune is False)."""
     import torch
 
     import paper_cs_0103001_gb300 as gb
@@ -506,7 +543,8 @@ def variant_batched(count: int = 512, steps: int = 5):
     th = [torch.from_numpy(h).cuda() for _, h, _ in batch]
     to = [torch.empty_like(a) for a in ti]
     plan = gb.Plan2DBatched([tuple(a.shape) for a in ti], "cuda")
-    plan.autotune(ti, th, to)
+    if autotune:
+        plan.autotune(ti, th, to)
     ms = _timed(lambda: plan.filter(ti, th, to), steps, 2)
     px = sum(a.numel() for a in ti)
     return {"images": count, "pixels": px, "ms": round(ms, 3), "images_per_s": round(count / (ms * 1e-3), 1),
@@ -681,7 +719,9 @@ def run_workload(args):
     if args.workload == "fft1d":
         res = variant_fft1d(args.log2n, args.dtype, args.steps, args.onchip)
     elif args.workload == "batched":
-        res = variant_batched(steps=args.steps)
+        res = variant_batched(count=args.count, steps=args.steps, autotune=args.autotune)
+    elif args.workload == "pipeline4096_tc":
+        res = variant_pipeline_tc(args.precision, args.steps)
     elif args.workload == "pipeline256":
         res = variant_pipeline256(args.steps)
     elif args.workload == "backward2048":
@@ -725,7 +765,12 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="gbfft", choices=["gbfft", "reference"])
     ap.add_argument("--workload", default="pipeline4096",
-                    choices=["pipeline4096", "fft1d", "batched", "pipeline256", "backward2048"])
+                    choices=["pipeline4096", "fft1d", "batched", "pipeline256", "backward2048", "pipeline4096_tc"])
+    ap.add_argument("--count", type=int, default=512, help="--workload batched: number of images")
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="--workload batched: launch shapes as planned, no tuning launches")
+    ap.add_argument("--precision", type=int, default=2, choices=[1, 2],
+                    help="--workload pipeline4096_tc: 1 = split BF16 x2 (3 products), 2 = x3 (6 products)")
     ap.add_argument("--log2n", type=int, default=20)
     ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
     ap.add_argument("--onchip", type=int, default=1, choices=[0, 1, 2],

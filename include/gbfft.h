@@ -119,7 +119,13 @@ typedef enum {
      * HBM read and one write instead of two each); 0 or 1 (default) = the
      * four-step passes, which are faster at these lengths.  Same results up
      * to rounding order. */
-    GBFFT_OPT_ONCHIP = 9
+    GBFFT_OPT_ONCHIP = 9,
+    /* 2D plans, the fused column pass over columns of 4096 rows: 0 (default)
+     * = the plan's choice (fft_plan_autotune's, else 1); 1 = persistent and
+     * TMA-fed, the filter column bulk-copied beside its column; 2 = the same
+     * with the filter read from global memory; 3 = one column per block.
+     * Same results; other heights have one form. */
+    GBFFT_OPT_COLUMN_FORM = 10
 } gbfft_option;
 
 /* Stages reported by gbfft_plan_profile_read. */
@@ -357,6 +363,14 @@ int gbfft_device_status(gbfft_plan_t plan);
  * next gbfft_device_status returns GBFFT_ERR_TIMEOUT.  Needs a bound
  * workspace; GBFFT_ERR_INVALID_VALUE for polls out of range. */
 int gbfft_selftest_wait_timeout(gbfft_plan_t plan, int64_t polls, gbfft_stream_t stream);
+
+/* Diagnostic (the paper has no counterpart): measures the GPU's FMA
+ * throughput, fp64 = 1 in double precision (the ALU roofline of the
+ * complex128 transforms), 0 in single precision.  Runs a few short launches
+ * of independent FMA chains on `stream` (all SMs) and waits for them; writes
+ * the best rate in FLOP/s (2 per FMA) to *flops_per_s.  Allocates nothing.
+ * GBFFT_ERR_NULL for a NULL output, GBFFT_ERR_INVALID_VALUE for fp64 not 0/1. */
+int gbfft_measure_fma_peak(int fp64, double *flops_per_s, gbfft_stream_t stream);
 
 /* Library version as 10000*major + 100*minor + patch. */
 int gbfft_version(void);

@@ -20,7 +20,7 @@ import importlib
 
 __all__ = ["fft", "ifft", "fft2_filter_ifft2", "fft2_filter_ifft2_analytic", "fft2_filter_ifft2_batched",
            "fft2_filter_ifft2_padded", "fft2_filter_ifft2_sharded", "fft2_spectrum", "Plan1D", "Plan2D",
-           "Plan2DBatched", "Plan2DSlab", "clear_plan_cache"]
+           "Plan2DBatched", "Plan2DSlab", "clear_plan_cache", "measure_fma_peak"]
 
 
 def __getattr__(name):

@@ -39,6 +39,7 @@ OPT_ENABLE_BACKWARD = 6
 OPT_BLOCKS_PER_SM = 7
 OPT_USE_GRAPH = 8
 OPT_ONCHIP = 9
+OPT_COLUMN_FORM = 10
 
 # gbfft_filter_kind
 FILTER_GAUSSIAN = 1
@@ -83,6 +84,7 @@ SIGNATURES = {
     "gbfft_last_cuda_error": (_INT, []),
     "gbfft_plan_profile_read": (_INT, [_P, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64), _INT]),
     "gbfft_version": (_INT, []),
+    "gbfft_measure_fma_peak": (_INT, [_INT, ctypes.POINTER(ctypes.c_double), _P]),
 }
 
 

@@ -249,6 +249,16 @@ class Plan2DSlab(_PlanBase):
             nat.call("fft2_slab_rows_inverse", self.handle, _ptr(back), _ptr(out), _stream_handle(self.device))
 
 
+def measure_fma_peak(fp64: bool, device=None) -> float:
+    """FMA throughput of the GPU in FLOP/s (2 per FMA), double or single
+    precision, measured by the library's diagnostic kernel."""
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    v = ctypes.c_double()
+    with torch.cuda.device(dev):
+        nat.call("gbfft_measure_fma_peak", 1 if fp64 else 0, ctypes.byref(v), _stream_handle(dev))
+    return float(v.value)
+
+
 _cache: dict[tuple, _PlanBase] = {}
 _cache_lock = threading.Lock()
 

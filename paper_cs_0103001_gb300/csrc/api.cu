@@ -67,6 +67,7 @@ struct gbfft_plan {
     int64_t opt_bps[kBatchStages] = {0, 0, 0, 0};  // blocks per SM per stage (0 = as many as fit)
     int64_t opt_graph = 1;
     int64_t opt_onchip = 1;
+    int64_t opt_colform = 0;  // column-pass form (GBFFT_OPT_COLUMN_FORM)
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
@@ -303,15 +304,34 @@ int batched_grid(gbfft_plan *p, int st, cudaError_t *err) {
     return bps * sm_count();
 }
 
+cudaError_t ensure_aux(gbfft_plan *p) {
+    cudaError_t e = cudaSuccess;
+    if (!p->aux) e = cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking);
+    if (e == cudaSuccess && !p->ev_fork) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
+    if (e == cudaSuccess && !p->ev_join) e = cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming);
+    return e;
+}
+
+// The four stages of a batched plan: the filter preparation on the plan's side
+// stream beside the forward row pass (it touches no spectrum), joined before
+// the column pass; under stream capture the side stream joins the capture.
 cudaError_t batched_launch_all(gbfft_plan *p, const gbfft_image_ptrs *ptrs, cudaStream_t s, const int *grid) {
     const BatchImage *imgs = reinterpret_cast<const BatchImage *>(p->ws + p->off_bimgs);
-    for (int st : kBatchOrder) {
+    auto stage = [&](int st, cudaStream_t on) {
         const BatchItem *items = reinterpret_cast<const BatchItem *>(p->ws + p->off_bitems[st]);
-        cudaError_t e = launch_batched_stage(st, grid[st], p->bsmem[st], imgs, items, (int)p->bitems[st].size(), ptrs,
-                                             p->ws, s);
-        if (e != cudaSuccess) return e;
-    }
-    return cudaSuccess;
+        return launch_batched_stage(st, grid[st], p->bsmem[st], imgs, items, (int)p->bitems[st].size(), ptrs, p->ws,
+                                    on);
+    };
+    cudaError_t e = ensure_aux(p);
+    if (e == cudaSuccess) e = cudaEventRecord(p->ev_fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->aux, p->ev_fork, 0);
+    if (e == cudaSuccess) e = stage(3, p->aux);  // filter preparation
+    if (e == cudaSuccess) e = cudaEventRecord(p->ev_join, p->aux);
+    if (e == cudaSuccess) e = stage(0, s);  // forward rows
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->ev_join, 0);
+    if (e == cudaSuccess) e = stage(1, s);  // columns
+    if (e == cudaSuccess) e = stage(2, s);  // inverse rows
+    return e;
 }
 
 void drop_graph(gbfft_plan *p) {
@@ -428,6 +448,10 @@ int fft_plan_set_option(gbfft_plan_t p, int key, int64_t value) {
             p->opt_backward = value;
             layout(p);
             return GBFFT_OK;
+        case GBFFT_OPT_COLUMN_FORM:
+            if ((p->kind != KIND_2D && p->kind != KIND_SLAB) || value < 0 || value > 3) return GBFFT_ERR_INVALID_VALUE;
+            p->opt_colform = value;
+            return GBFFT_OK;
         default: return GBFFT_ERR_INVALID_VALUE;
     }
 }
@@ -499,13 +523,6 @@ int fft_inverse(gbfft_plan_t p, const void *in, void *out, gbfft_stream_t stream
     return run_1d(p, in, out, +1, reinterpret_cast<cudaStream_t>(stream));
 }
 
-static cudaError_t ensure_aux(gbfft_plan *p) {
-    cudaError_t e = cudaSuccess;
-    if (!p->aux) e = cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking);
-    if (e == cudaSuccess && !p->ev_fork) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
-    if (e == cudaSuccess && !p->ev_join) e = cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming);
-    return e;
-}
 
 // One chunk of the Sec. 5 pipeline: filter preparation on the side stream
 // while the forward row pass runs, then the fused column pass and the inverse
@@ -568,7 +585,8 @@ static int pipeline_chunk(gbfft_plan *p, const float *img, const float *H, float
     rc = launch(p, GBFFT_STAGE_COLS, s, [&] {
         return terms ? launch_cols_tc(spec, hs, beta, hs_img, beta_img, rows, cols, nb, p->ws + p->off_tw1, terms, s)
                      : launch_cols_filter(spec, hs, beta, hs_img, beta_img, rows, cols, nb, p->ws + p->off_tw1,
-                                                          reinterpret_cast<int *>(p->ws + p->off_status), s);
+                                          reinterpret_cast<int *>(p->ws + p->off_status), s, ColSlab{0, 0, 0},
+                                          (int)p->opt_colform);
     });
     if (rc) return rc;
     return launch(p, GBFFT_STAGE_ROWS_INV, s, [&] {
@@ -819,7 +837,7 @@ int fft2_slab_columns(gbfft_plan_t p, void *recv, const float *H, gbfft_stream_t
     return launch(p, GBFFT_STAGE_COLS, s, [&] {
         return launch_cols_filter(recv, hs, beta, 0, 0, rows, cols, 1, p->ws + p->off_tw1,
                                   reinterpret_cast<int *>(p->ws + p->off_status), s,
-                                  ColSlab{ilog2_exact(ld), mloc, kbase});
+                                  ColSlab{ilog2_exact(ld), mloc, kbase}, (int)p->opt_colform);
     });
 }
 
@@ -910,7 +928,11 @@ int fft2_filter_ifft2_batched(gbfft_plan_t p, const gbfft_image_ptrs *images, gb
         grid[st] = batched_grid(p, st, &e);
         if (e != cudaSuccess) return cuda_fail(e);
     }
-    if (!p->opt_graph) {
+    if (!p->opt_graph && !p->opt_profile) {
+        e = batched_launch_all(p, images, s, grid);
+        return e == cudaSuccess ? GBFFT_OK : cuda_fail(e);
+    }
+    if (!p->opt_graph) {  // profiling: every stage alone on the caller's stream
         for (int st : kBatchOrder) {
             const int stage = st == 0   ? GBFFT_STAGE_ROWS_FWD
                               : st == 1 ? GBFFT_STAGE_COLS
@@ -1025,6 +1047,7 @@ int fft_plan_get_option(gbfft_plan_t p, int key, int64_t *value) {
             return GBFFT_OK;
         case GBFFT_OPT_USE_GRAPH: *value = p->opt_graph; return GBFFT_OK;
         case GBFFT_OPT_ONCHIP: *value = p->opt_onchip; return GBFFT_OK;
+        case GBFFT_OPT_COLUMN_FORM: *value = p->opt_colform; return GBFFT_OK;
         default: return GBFFT_ERR_INVALID_VALUE;
     }
 }

@@ -118,13 +118,19 @@ cudaError_t launch_cols_spectrum(const void *spec, float *mag_T, float *nyq, flo
 // runs of `crows` rows, run q at row q * cstride + c * crows (one image); the
 // runs land back to back in the buffer, so the slot order in shared memory is
 // the same.  One image: nchunk = 1, crows = N/16.
-template <int N> struct ColTmaCfg {
+// Two forms: the filter column bulk-copied beside its column (GF = false),
+// or read from global memory (L2) after the forward transform (GF = true),
+// which leaves more of the SM's memory to the L1 cache.  Two blocks per SM
+// (BL): a third needs 80 registers per thread and spills (73 against 45 us at
+// 4096^2, measured), so it is not offered.
+template <int N, bool GF = false, int BL = 2> struct ColTmaCfg {
     typedef ColCfg<N> C;
     static constexpr int E = C::E, T = C::T, THREADS = C::THREADS;
     static_assert(C::W == 1 && T >= 64, "one column per block, slot rows aligned to the swizzle");
     static constexpr int ROWS = N / 16;
+    static constexpr int BLOCKS = BL;  // per SM
     static constexpr size_t BUF = ((size_t)padded_len(N) * sizeof(float2) + 1023) / 1024 * 1024;
-    static constexpr size_t FB = (size_t)N * sizeof(float);
+    static constexpr size_t FB = GF ? 0 : (size_t)N * sizeof(float);
     static constexpr size_t SMEM = 1024 + 2 * BUF + 2 * FB + 32;  // alignment slack, buffers, 2 mbarriers
 };
 
@@ -138,13 +144,13 @@ __device__ __forceinline__ int swz128(int s) {
 // slot reads to the issue of its tensor stores.  Out of line: compiled on its
 // own, so nothing of one column (twiddles, addresses) is kept in registers
 // across the loop over columns.
-template <int N>
+template <int N, bool GF, int BL>
 __device__ __noinline__ void cols_tma_column(const CUtensorMap *map, float2 *bf, const float *h,
                                              const float *bt, long long c, bool col0, bool prefetch, int b,
                                              const float2 *__restrict__ tw, int log2g, unsigned char *base,
                                              const float *hs, long long hs_img, int log2half, int crows,
                                              int boxr, long long cstride, int nchunk) {
-    typedef ColTmaCfg<N> K;
+    typedef ColTmaCfg<N, GF, BL> K;
     constexpr int E = K::E, T = K::T;
     const int t = threadIdx.x;
     const int G = 1 << log2g;
@@ -165,11 +171,13 @@ __device__ __noinline__ void cols_tma_column(const CUtensorMap *map, float2 *bf,
         float *nf = reinterpret_cast<float *>(base + 2 * K::BUF + (b ^ 1) * K::FB);
         uint64_t *bar = reinterpret_cast<uint64_t *>(base + 2 * K::BUF + 2 * K::FB) + (b ^ 1);
         bulk_wait_read();  // the other buffer's stores have read it
-        mbar_expect_tx(bar, (uint32_t)(N * sizeof(float2) + N * sizeof(float)));
+        mbar_expect_tx(bar, (uint32_t)(N * sizeof(float2) + K::FB));
         for (int q = 0; q < nchunk; ++q)
             for (int r = 0; r < crows; r += boxr)
                 tma_load_2d(nb + (q * crows + r) * 16, map, 0, (int)(q * cstride + cn * crows + r), bar);
-        bulk_load(nf, hs + (cn >> log2half) * hs_img + (cn & ((1LL << log2half) - 1)) * N, N * sizeof(float), bar);
+        if constexpr (!GF)
+            bulk_load(nf, hs + (cn >> log2half) * hs_img + (cn & ((1LL << log2half) - 1)) * N, N * sizeof(float),
+                      bar);
     }
     // the first exchange starts with a block barrier: every thread has read
     // its slots before the buffer becomes the exchange buffer
@@ -183,12 +191,12 @@ __device__ __noinline__ void cols_tma_column(const CUtensorMap *map, float2 *bf,
         for (int e = 0; e < E; ++e) {
             const int u = t + T * e;
             const float2 qm = bf[pad16((N - u) & (N - 1))];
-            const float hu = h[u], bu = bt[u];
+            const float hu = GF ? __ldg(h + u) : h[u], bu = bt[u];
             v[e] = make_float2(hu * v[e].x + bu * qm.x, hu * v[e].y - bu * qm.y);
         }
     } else {
 #pragma unroll
-        for (int e = 0; e < E; ++e) v[e] = cscale(v[e], h[t + T * e]);
+        for (int e = 0; e < E; ++e) v[e] = cscale(v[e], GF ? __ldg(h + t + T * e) : h[t + T * e]);
     }
     fft_regs<N, E, 1>(v, bf, tw, t);
     __syncthreads();  // the last exchange's reads are complete
@@ -204,13 +212,13 @@ __device__ __noinline__ void cols_tma_column(const CUtensorMap *map, float2 *bf,
     }
 }
 
-template <int N>
-__global__ void __launch_bounds__(ColCfg<N>::THREADS, 2)
+template <int N, bool GF, int BL>
+__global__ void __launch_bounds__(ColCfg<N>::THREADS, BL)
     k_cols_filter_tma(const __grid_constant__ CUtensorMap map, const float *__restrict__ hs,
                       const float *__restrict__ beta, long long hs_img, long long beta_img, int log2half,
                       long long ncols, int log2g, const float2 *__restrict__ tw, int *status, int crows, int boxr,
                       long long cstride, int nchunk, int kbase) {
-    typedef ColTmaCfg<N> K;
+    typedef ColTmaCfg<N, GF, BL> K;
     extern __shared__ __align__(1024) unsigned char smraw[];
     unsigned char *base = smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u);  // the swizzle repeats every 1 KB
     uint64_t *bar = reinterpret_cast<uint64_t *>(base + 2 * K::BUF + 2 * K::FB);
@@ -223,12 +231,14 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, 2)
     __syncthreads();
     long long c = blockIdx.x;
     if (t == 0 && c < ncols) {  // the first column and its filter into buffer 0
-        mbar_expect_tx(&bar[0], (uint32_t)(N * sizeof(float2) + N * sizeof(float)));
+        mbar_expect_tx(&bar[0], (uint32_t)(N * sizeof(float2) + K::FB));
         float2 *b0 = reinterpret_cast<float2 *>(base);
         for (int q = 0; q < nchunk; ++q)
             for (int r = 0; r < crows; r += boxr)
                 tma_load_2d(b0 + (q * crows + r) * 16, &map, 0, (int)(q * cstride + c * crows + r), &bar[0]);
-        bulk_load(base + 2 * K::BUF, hs + (c >> log2half) * hs_img + (c & hmask) * N, N * sizeof(float), &bar[0]);
+        if constexpr (!GF)
+            bulk_load(base + 2 * K::BUF, hs + (c >> log2half) * hs_img + (c & hmask) * N, N * sizeof(float),
+                      &bar[0]);
     }
     for (int it = 0; c < ncols; c += gridDim.x, ++it) {
         const int b = it & 1;
@@ -240,8 +250,9 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, 2)
             }
             break;
         }
-        cols_tma_column<N>(&map, reinterpret_cast<float2 *>(base + b * K::BUF),
-                           reinterpret_cast<const float *>(base + 2 * K::BUF + b * K::FB),
+        const float *h = GF ? hs + (c >> log2half) * hs_img + (c & hmask) * N  // this column's filter
+                            : reinterpret_cast<const float *>(base + 2 * K::BUF + b * K::FB);
+        cols_tma_column<N, GF, BL>(&map, reinterpret_cast<float2 *>(base + b * K::BUF), h,
                            beta + (c >> log2half) * beta_img, c, kbase == 0 && (c & hmask) == 0,
                            c + gridDim.x < ncols, b, tw, log2g, base, hs, hs_img, log2half, crows, boxr, cstride,
                            nchunk);
@@ -249,11 +260,11 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, 2)
     if (t == 0) bulk_wait_read();  // every store has read its buffer before the block's memory goes
 }
 
-template <int N>
+template <int N, bool GF, int BL>
 static cudaError_t run_cols_tma(void *spec, const float *hs, const float *beta, long long hs_img, long long beta_img,
                                 int cols, int nimg, int log2g, const void *tw, int *status, cudaStream_t s,
                                 bool *used, ColSlab cs) {
-    typedef ColTmaCfg<N> K;
+    typedef ColTmaCfg<N, GF, BL> K;
     *used = false;
     const EncodeTiledFn enc = encode_tiled();
     if (!enc || !status || hs_img % 4 != 0) return cudaSuccess;
@@ -276,10 +287,10 @@ static cudaError_t run_cols_tma(void *spec, const float *hs, const float *beta, 
             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return cudaSuccess;
-    auto kern = k_cols_filter_tma<N>;
+    auto kern = k_cols_filter_tma<N, GF, BL>;
     static int slots = 0;  // resident blocks (per process; one device type)
     if (slots == 0) {
-        cudaError_t e = set_smem_attrs((const void *)kern, K::SMEM, 2);
+        cudaError_t e = set_smem_attrs((const void *)kern, K::SMEM, K::BLOCKS);
         int dev = 0, sms = 0, per_sm = 0;
         if (e == cudaSuccess) e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -298,15 +309,22 @@ static cudaError_t run_cols_tma(void *spec, const float *hs, const float *beta, 
     return cudaGetLastError();
 }
 
+// form: 0 = the default (the TMA-fed persistent kernel with its filter in
+// shared memory where it applies), 1 = that kernel, 2 = the TMA-fed kernel
+// with the filter read from global memory, 3 = the one-column-per-block kernel.
 template <int N>
 static cudaError_t run_cols(void *spec, const float *hs, const float *beta, long long hs_img, long long beta_img,
-                            int cols, int nimg, int log2g, const void *tw, int *status, cudaStream_t s, ColSlab cs) {
+                            int cols, int nimg, int log2g, const void *tw, int *status, cudaStream_t s, ColSlab cs,
+                            int form) {
     typedef ColCfg<N> K;
     if constexpr (N >= 4096 && K::W == 1 && K::THREADS == 256) {
-        if ((1 << log2g) <= K::T && cols >= 4) {
+        if ((1 << log2g) <= K::T && cols >= 4 && form != 3) {
             bool used = false;
             cudaError_t e =
-                run_cols_tma<N>(spec, hs, beta, hs_img, beta_img, cols, nimg, log2g, tw, status, s, &used, cs);
+                form == 2 ? run_cols_tma<N, true, 2>(spec, hs, beta, hs_img, beta_img, cols, nimg, log2g, tw, status, s,
+                                                     &used, cs)
+                          : run_cols_tma<N, false, 2>(spec, hs, beta, hs_img, beta_img, cols, nimg, log2g, tw, status,
+                                                      s, &used, cs);
             if (e != cudaSuccess || used) return e;
         }
     }
@@ -368,13 +386,15 @@ cudaError_t launch_cols_analytic(void *spec, int kind, double p0, double p1, int
 
 cudaError_t launch_cols_filter(void *spec, const float *hs, const float *beta, long long hs_img, long long beta_img,
                                int rows, int cols, int nimg, const void *tw_rows, int *status, cudaStream_t s,
-                               ColSlab cs) {
+                               ColSlab cs, int form) {
     int g = rows_pairs_per_block(cols);
     if (g > rows / 2) g = rows / 2;
     const int log2g = ilog2(g);
     switch (ilog2(rows)) {
-#define GBFFT_CASE(L) \
-    case L: return run_cols<(1 << L)>(spec, hs, beta, hs_img, beta_img, cols, nimg, log2g, tw_rows, status, s, cs);
+#define GBFFT_CASE(L)                                                                                        \
+    case L:                                                                                                  \
+        return run_cols<(1 << L)>(spec, hs, beta, hs_img, beta_img, cols, nimg, log2g, tw_rows, status, s, cs, \
+                                  form);
         GBFFT_CASE(1) GBFFT_CASE(2) GBFFT_CASE(3) GBFFT_CASE(4) GBFFT_CASE(5) GBFFT_CASE(6) GBFFT_CASE(7)
         GBFFT_CASE(8) GBFFT_CASE(9) GBFFT_CASE(10) GBFFT_CASE(11) GBFFT_CASE(12) GBFFT_CASE(13)
 #undef GBFFT_CASE

@@ -94,10 +94,12 @@ cudaError_t launch_cols_analytic(void *spec, int kind, double p0, double p1, int
 // hs_img / beta_img: elements between images' prepared filters (0 = shared)
 // With cs.ls > 0 (one image): the column block of a decomposed image, spec in
 // the received layout [ranks][cs.mloc][2^cs.ls] (layout.cuh, ColSlab), hs the
-// prepared filter of those columns only.
+// prepared filter of those columns only.  form (columns of 4096 rows): 0 =
+// default, 1 = TMA-fed with the filter in shared memory, 2 = TMA-fed with the
+// filter read from global memory, 3 = one column per block.
 cudaError_t launch_cols_filter(void *spec, const float *hs, const float *beta, long long hs_img, long long beta_img,
                                int rows, int cols, int nimg, const void *tw_rows, int *status, cudaStream_t s,
-                               ColSlab cs = ColSlab{0, 0, 0});
+                               ColSlab cs = ColSlab{0, 0, 0}, int form = 0);
 cudaError_t launch_rows_inv(const void *spec, float *out, int rows, int cols, int nimg, const void *tw_cols,
                             int *status, cudaStream_t s, Slab slab = Slab{0, 0});
 // Tensor-core variants (tc2d.cu): radix-16 passes as split-BF16 DFT-matrix

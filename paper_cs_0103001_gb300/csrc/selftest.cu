@@ -1,10 +1,12 @@
-// selftest.cu — a diagnostic of the bounded asynchronous-copy waits.
+// selftest.cu — diagnostics: the bounded asynchronous-copy waits, and the
+// FMA throughput of the GPU (the ALU roofline of the FP64 transforms).
 //
 // The TMA-fed kernels (four-step passes, column pass) wait on an mbarrier for
 // their copies a bounded number of times and, if the copies never complete,
 // record a timeout in the plan's device status word and return instead of
 // hanging.  This kernel exercises that path on purpose: it arms an mbarrier
 // for 16 bytes that no copy will ever deliver, so its bounded wait runs out.
+#include "gbfft.h"
 #include "internal.h"
 #include "tma.cuh"
 
@@ -23,4 +25,57 @@ cudaError_t launch_wait_timeout(int *status, unsigned polls, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Eight independent FMA chains per thread, `iters` steps each; the chains
+// stay bounded (|m| < 1) and their sum is stored only in a case that does not
+// happen, which keeps them live.
+__device__ double g_fma_sink;
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_peak(T m, T a, int iters) {
+    T x[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) x[i] = (T)(threadIdx.x + i) * (T)1e-3;
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) x[i] = fma(x[i], m, a);
+    }
+    T s = 0;
+#pragma unroll
+    for (int i = 0; i < 8; ++i) s += x[i];
+    if (s == (T)-12345.0) g_fma_sink = (double)s;
+}
+
 }  // namespace gbfft
+
+extern "C" int gbfft_measure_fma_peak(int fp64, double *flops_per_s, gbfft_stream_t stream) {
+    using namespace gbfft;
+    if (!flops_per_s) return GBFFT_ERR_NULL;
+    if (fp64 != 0 && fp64 != 1) return GBFFT_ERR_INVALID_VALUE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    const int blocks = sms * 4, threads = 256;
+    const int iters = fp64 ? 1024 : 8192;
+    float best = 0.f;
+    for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+        e = cudaEventRecord(a, s);
+        if (fp64)
+            k_fma_peak<double><<<blocks, threads, 0, s>>>(0.999999, 1e-3, iters);
+        else
+            k_fma_peak<float><<<blocks, threads, 0, s>>>(0.9999f, 1e-3f, iters);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaEventRecord(b, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        if (e == cudaSuccess && rep > 0 && (best == 0.f || ms < best)) best = ms;  // first launch warms up
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    if (e != cudaSuccess) return GBFFT_ERR_CUDA;
+    *flops_per_s = 2.0 * 8.0 * iters * (double)blocks * threads / (best * 1e-3);
+    return GBFFT_OK;
+}

@@ -134,3 +134,20 @@ def test_workload_sizes(gb, cfg):
             px = np.sum(F * np.exp(2j * np.pi * (np.arange(rows)[:, None] * x / rows
                                                  + np.arange(cols)[None, :] * y / cols))).real
             assert abs(got[x, y] - px) <= 1e-5 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("form", [0, 1, 2, 3])
+@pytest.mark.parametrize("rows,cols,batch", [(4096, 64, 3), (4096, 1024, 1)])
+def test_column_pass_forms(gb, form, rows, cols, batch):
+    """Each form of the column pass over 4096-row columns (GBFFT_OPT_COLUMN_FORM:
+    TMA-fed with the filter in shared or global memory, one column per block)
+    against the oracle, with per-image filters over several images."""
+    import torch
+
+    from paper_cs_0103001_gb300 import _native as nat
+
+    img = np.stack([synth.sky(rows, cols, 60, 15, b) for b in range(batch)])
+    H = np.stack([synth.random_filter(rows, cols, 16, b) for b in range(batch)])
+    plan = gb.Plan2D(rows, cols, batch, "cuda", {nat.OPT_H_BATCH_STRIDE: rows * cols, nat.OPT_COLUMN_FORM: form})
+    out = plan.filter(torch.from_numpy(img).cuda(), torch.from_numpy(H).cuda()).cpu().numpy()
+    assert max_rel_l2(out, oracle.pipeline(img, H), axes=(1, 2)) <= tol_fp32(rows * cols)
