@@ -225,6 +225,9 @@ def run_gbfft(args):
     out = torch.empty_like(img)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     plan = gb.Plan2D(ROWS, COLS, 1, dev)
+    # the library's autotuner picks the plan's configuration (cached per GPU
+    # and shape, so only the first run on a machine times the candidates)
+    tuning = plan.autotune(img, H, out)
     stream = torch.cuda.current_stream(dev)
 
     def step():
@@ -429,7 +432,9 @@ def run_gbfft(args):
                             "copies overlapped with compute on three streams; copies_only = the same two "
                             "copies per step with no compute (the host link's ceiling)"},
             "gpu_launches": int(round(launches_per_step * args.steps)),
+            "tuning": tuning,
             "variants": dict(run_variants(), pipeline4096_precision=_guard(lambda: variant_precision(img, H, ref, flush)),
+                             pipeline4096_column_forms=_guard(lambda: variant_column_forms(img, H, flush)),
                              pipeline4096_analytic_filter=_guard(lambda: variant_analytic(img, flush)),
                              cufft_context=_guard(lambda: variant_cufft_context(img, H, ref, flush)))
             if args.variants else None,
@@ -570,6 +575,22 @@ def variant_precision(img, H, ref, flush, steps: int = 100):
         res[name] = {"us": round(ms * 1e3, 2),
                      "rel_l2": float(np.linalg.norm(got - ref) / np.linalg.norm(ref))}
     return res
+
+
+def variant_column_forms(img, H, flush, steps: int = 100):
+    """The headline workload with each form of the column pass
+    (GBFFT_OPT_COLUMN_FORM), the candidates the autotuner chooses among."""
+    import torch
+
+    import paper_cs_0103001_gb300 as gb
+    from paper_cs_0103001_gb300 import _native as nat
+
+    out = torch.empty_like(img)
+    res = {}
+    for name, form in (("tma_filter_in_shared_memory", 1), ("tma_filter_from_global", 2), ("one_column_per_block", 3)):
+        plan = gb.Plan2D(img.shape[0], img.shape[1], 1, img.device, {nat.OPT_COLUMN_FORM: form})
+        res[name] = round(_timed(lambda: plan.filter(img, H, out=out), steps, 5, flush) * 1e3, 2)
+    return {"us": res}
 
 
 def variant_cufft_context(img, H, ref, flush, steps: int = 100):

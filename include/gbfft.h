@@ -324,10 +324,33 @@ int fft2_batched_plan_create(int count, const int64_t *rows, const int64_t *cols
  * CUDA graph (on a private stream) and replayed on `stream`. */
 int fft2_filter_ifft2_batched(gbfft_plan_t plan, const gbfft_image_ptrs *images, gbfft_stream_t stream);
 
-/* Tune a plan's launch shapes by timing candidates on `stream` (blocking).
- * Batched plans: blocks per SM of each stage, `args` = the device image
- * array of fft2_filter_ifft2_batched (the outputs are written).  Other plans
- * have nothing to tune and return GBFFT_OK. */
+/* Device buffers the autotuner runs a 1D or 2D plan on (host struct):
+ * 1D: in, out as for fft_forward (H unused); 2D: in = img, H, out as for
+ * fft2_filter_ifft2.  `out` is written. */
+typedef struct {
+    const void *in;
+    const float *H;
+    void *out;
+} gbfft_tune_args;
+
+/* Tune a plan by timing its candidate configurations on `stream` (blocking;
+ * each candidate's median of 7 runs; a later candidate replaces an earlier
+ * one only if more than 1 % faster, so ties keep the default) and keep the
+ * fastest in the plan's options:
+ *   2D plans: GBFFT_OPT_COLUMN_FORM for columns of 4096 rows, and
+ *     GBFFT_OPT_ONCHIP (on-chip or three-pass) for sides <= 256;
+ *     args = a gbfft_tune_args.
+ *   1D plans: the one-cluster path against the four-step passes for complex64
+ *     lengths 2^15..2^17 (GBFFT_OPT_ONCHIP); args = a gbfft_tune_args.
+ *   Batched plans: blocks per SM of each stage (GBFFT_OPT_BLOCKS_PER_SM);
+ *     args = the device image array of fft2_filter_ifft2_batched.
+ *   Slab plans: nothing to tune (GBFFT_OK).
+ * Results are cached in a JSON file keyed by the GPU's name and SM count and
+ * the plan's shape: a later call for the same key applies the stored choice
+ * without timing.  The file is $GBFFT_TUNE_CACHE (empty: no cache), else
+ * $XDG_CACHE_HOME/gbfft/tune.json or $HOME/.cache/gbfft/tune.json; a file
+ * that cannot be read or written only means tuning again.  Every candidate
+ * computes the same result (up to rounding order). */
 int fft_plan_autotune(gbfft_plan_t plan, const void *args, gbfft_stream_t stream);
 
 /* Read back an option (GBFFT_OPT_IMAGES_PER_CHUNK gives the chunk in use). */

@@ -37,6 +37,12 @@ def _require_cuda(t: torch.Tensor, what: str) -> None:
         raise ValueError(f"{what} must be a CUDA tensor (gbfft has no CPU path)")
 
 
+class _TuneArgs(ctypes.Structure):
+    """gbfft_tune_args: the device buffers fft_plan_autotune runs a plan on."""
+
+    _fields_ = [("in_", _P), ("H", _P), ("out", _P)]
+
+
 class _PlanBase:
     """Owns a gbfft plan handle and its workspace tensor."""
 
@@ -68,6 +74,16 @@ class _PlanBase:
         """Launch the diagnostic block whose bounded wait runs out (sets this
         plan's device status word; see gbfft_selftest_wait_timeout)."""
         nat.call("gbfft_selftest_wait_timeout", self.handle, polls, _stream_handle(self.device))
+
+    def get_option(self, key: int) -> int:
+        v = ctypes.c_int64()
+        nat.call("fft_plan_get_option", self.handle, int(key), ctypes.byref(v))
+        return int(v.value)
+
+    def _autotune(self, x: torch.Tensor, H: torch.Tensor | None, out: torch.Tensor) -> None:
+        args = _TuneArgs(_P(x.data_ptr()), _P(H.data_ptr()) if H is not None else _P(), _P(out.data_ptr()))
+        with self.lock:
+            nat.call("fft_plan_autotune", self.handle, ctypes.byref(args), _stream_handle(self.device))
 
     def profile_read(self) -> dict[str, tuple[float, int]]:
         n = len(nat.STAGES)
@@ -101,6 +117,15 @@ class Plan1D(_PlanBase):
     def inverse(self, x: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
         return self._run("fft_inverse", x, out)
 
+    def autotune(self, x: torch.Tensor, out: torch.Tensor | None = None) -> int:
+        """Time the plan's candidate paths on x (forward transforms into out)
+        and keep the fastest (cached per GPU and shape); returns
+        GBFFT_OPT_ONCHIP as chosen."""
+        if out is None:
+            out = torch.empty_like(x)
+        self._autotune(x, None, out)
+        return self.get_option(nat.OPT_ONCHIP)
+
     def _run(self, fn: str, x: torch.Tensor, out: torch.Tensor | None) -> torch.Tensor:
         if x.dtype != self.dtype or x.numel() != self.n * self.batch or not x.is_contiguous():
             raise ValueError("input does not match the plan (dtype, size, contiguity)")
@@ -127,6 +152,14 @@ class Plan2D(_PlanBase):
         with self.lock:
             nat.call("fft2_filter_ifft2", self.handle, _ptr(img), _ptr(H), _ptr(out), _stream_handle(img.device))
         return out
+
+    def autotune(self, img: torch.Tensor, H: torch.Tensor, out: torch.Tensor | None = None) -> dict[str, int]:
+        """Time the plan's candidate configurations on these buffers and keep
+        the fastest (cached per GPU and shape); returns the chosen options."""
+        if out is None:
+            out = torch.empty_like(img)
+        self._autotune(img, H, out)
+        return {"column_form": self.get_option(nat.OPT_COLUMN_FORM), "onchip": self.get_option(nat.OPT_ONCHIP)}
 
     def filter_padded(self, img: torch.Tensor, H: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
         """Images [..., r, c] with r <= rows, c <= cols, zero-padded to the

@@ -8,10 +8,14 @@
 #include <new>
 #include <vector>
 
+#include <cstdio>
+#include <string>
+
 #include "batched.h"
 #include "gbfft.h"
 #include "internal.h"
 #include "tma.cuh"
+#include "tune.h"
 
 using namespace gbfft;
 
@@ -975,14 +979,157 @@ int fft2_filter_ifft2_batched(gbfft_plan_t p, const gbfft_image_ptrs *images, gb
     return launch(p, GBFFT_STAGE_GRAPH, s, [&] { return cudaGraphLaunch(p->graph_exec, s); });
 }
 
-int fft_plan_autotune(gbfft_plan_t p, const void *args, gbfft_stream_t stream) {
-    if (!p) return GBFFT_ERR_NULL;
-    if (p->kind != KIND_BATCH) return GBFFT_OK;  // nothing tunable beyond the defaults
-    int rc = check_plan_ready(p);
-    if (rc) return rc;
-    if (!args) return GBFFT_ERR_NULL;
-    const gbfft_image_ptrs *images = static_cast<const gbfft_image_ptrs *>(args);
-    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+}  // extern "C"
+
+// ---- autotuner ---------------------------------------------------------
+
+namespace {
+
+// Median of `reps` timed runs of f on s (one untimed run first), in ms.
+template <typename F>
+cudaError_t time_median(cudaStream_t s, int reps, F &&f, float *ms_out) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    std::vector<float> t;
+    if (e == cudaSuccess && f() != GBFFT_OK) e = cudaErrorUnknown;
+    for (int r = 0; r < reps && e == cudaSuccess; ++r) {
+        e = cudaEventRecord(a, s);
+        if (e == cudaSuccess && f() != GBFFT_OK) e = cudaErrorUnknown;
+        if (e == cudaSuccess) e = cudaEventRecord(b, s);
+        if (e == cudaSuccess) e = cudaEventSynchronize(b);
+        float ms = 0.f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+        t.push_back(ms);
+    }
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    if (e == cudaSuccess) {
+        std::sort(t.begin(), t.end());
+        *ms_out = t[t.size() / 2];
+    }
+    return e;
+}
+
+std::string plan_signature(const gbfft_plan *p) {
+    char buf[160];
+    if (p->kind == KIND_1D) {
+        snprintf(buf, sizeof buf, "1d:n=%d:b=%lld:t=%d", p->log2n, (long long)p->batch, p->dtype);
+    } else if (p->kind == KIND_2D) {
+        snprintf(buf, sizeof buf, "2d:r=%d:c=%d:b=%lld:h=%d:p=%lld:bw=%lld", p->log2r, p->log2c, (long long)p->batch,
+                 p->opt_h_stride ? 1 : 0, (long long)p->opt_precision, (long long)p->opt_backward);
+    } else if (p->kind == KIND_BATCH) {
+        uint64_t h = 1469598103934665603ull;  // FNV-1a over the shapes
+        for (const BatchImage &im : p->bimgs) {
+            h = (h ^ (uint64_t)im.log2r) * 1099511628211ull;
+            h = (h ^ (uint64_t)im.log2c) * 1099511628211ull;
+        }
+        snprintf(buf, sizeof buf, "batch:n=%zu:h=%016llx", p->bimgs.size(), (unsigned long long)h);
+    } else {
+        snprintf(buf, sizeof buf, "slab:r=%d:c=%d:n=%d", p->log2r, p->log2c, p->nranks);
+    }
+    return std::string(buf);
+}
+
+// Apply a cached entry; false if it lacks what this plan kind tunes.
+bool apply_tuned(gbfft_plan *p, const TuneEntry &e) {
+    auto get = [&](const char *k, int64_t *v) {
+        auto it = e.find(k);
+        if (it == e.end()) return false;
+        *v = (int64_t)it->second;
+        return true;
+    };
+    if (p->kind == KIND_BATCH) {
+        int64_t v[kBatchStages];
+        for (int st = 0; st < kBatchStages; ++st) {
+            char k[8];
+            snprintf(k, sizeof k, "bps%d", st);
+            if (!get(k, &v[st]) || v[st] < 1 || v[st] > 64) return false;
+        }
+        for (int st = 0; st < kBatchStages; ++st) p->opt_bps[st] = v[st];
+        drop_graph(p);
+        return true;
+    }
+    int64_t form = 0, onchip = 0;
+    if (!get("column_form", &form) || !get("onchip", &onchip)) return false;
+    if (form < 0 || form > 3 || onchip < 0 || onchip > 2) return false;
+    p->opt_colform = form;
+    p->opt_onchip = onchip;
+    return true;
+}
+
+// 2D plans: the column-pass form (columns of 4096 rows) and the one-launch
+// on-chip path against the three-pass path (sides <= 256), timed on the
+// caller's image, filter and output.
+int tune_2d(gbfft_plan *p, const gbfft_tune_args *a, cudaStream_t s, TuneEntry &out) {
+    const int rows = 1 << p->log2r, cols = 1 << p->log2c;
+    std::vector<int> forms = {p->opt_colform ? (int)p->opt_colform : 1};
+    if (rows == 4096 && p->opt_precision == 0) forms = {1, 2, 3};
+    std::vector<int> onchips = {(int)p->opt_onchip};
+    if (p->opt_precision == 0 && onchip_supported(rows, cols)) onchips = {1, 0};
+    const float *img = static_cast<const float *>(a->in), *H = static_cast<const float *>(a->H);
+    float *o = static_cast<float *>(a->out);
+    float best = 0.f, first = 0.f;
+    int bf = forms[0], bo = onchips[0];
+    bool have = false;
+    for (int oc : onchips) {
+        for (int f : forms) {
+            if (oc && onchip_supported(rows, cols) && f != forms[0]) continue;  // the on-chip path has no column pass
+            p->opt_colform = f;
+            p->opt_onchip = oc;
+            float ms = 0.f;
+            cudaError_t e = time_median(
+                s, 7, [&] { return fft2_filter_ifft2(p, img, H, o, reinterpret_cast<gbfft_stream_t>(s)); }, &ms);
+            if (e != cudaSuccess) return cuda_fail(e);
+            if (!have) first = ms;
+            if (!have || ms < 0.99f * best) {  // a later candidate must win by more than 1 %
+                best = ms;
+                bf = f;
+                bo = oc;
+                have = true;
+            }
+        }
+    }
+    p->opt_colform = bf;
+    p->opt_onchip = bo;
+    out["column_form"] = bf;
+    out["onchip"] = bo;
+    out["us"] = 1e3 * best;
+    out["us_first_candidate"] = 1e3 * first;
+    return GBFFT_OK;
+}
+
+// 1D plans: the one-cluster path against the four-step passes (complex64
+// lengths 2^15 .. 2^17), timed on the caller's input and output.
+int tune_1d(gbfft_plan *p, const gbfft_tune_args *a, cudaStream_t s, TuneEntry &out) {
+    std::vector<int> onchips = {(int)p->opt_onchip};
+    if (p->log2n > max_single_log2(p) && fft1d_cluster_supported(p->log2n, is_dbl(p))) onchips = {1, 2};
+    float best = 0.f, first = 0.f;
+    int bo = onchips[0];
+    bool have = false;
+    for (int oc : onchips) {
+        p->opt_onchip = oc;
+        float ms = 0.f;
+        cudaError_t e = time_median(s, 7, [&] { return run_1d(p, a->in, a->out, -1, s); }, &ms);
+        if (e != cudaSuccess) return cuda_fail(e);
+        if (!have) first = ms;
+        if (!have || ms < 0.99f * best) {
+            best = ms;
+            bo = oc;
+            have = true;
+        }
+    }
+    p->opt_onchip = bo;
+    out["column_form"] = (double)p->opt_colform;
+    out["onchip"] = bo;
+    out["us"] = 1e3 * best;
+    out["us_first_candidate"] = 1e3 * first;
+    return GBFFT_OK;
+}
+
+// Batched plans: blocks per SM of each stage, each stage timed alone while
+// the others keep their current shape.
+int tune_batched(gbfft_plan *p, const gbfft_image_ptrs *images, cudaStream_t s, TuneEntry &out) {
     cudaEvent_t a = nullptr, b = nullptr;
     cudaError_t e = cudaEventCreate(&a);
     if (e == cudaSuccess) e = cudaEventCreate(&b);
@@ -1025,11 +1172,53 @@ int fft_plan_autotune(gbfft_plan_t p, const void *args, gbfft_stream_t stream) {
             }
         }
         p->opt_bps[st] = best_bps;
+        char k[8];
+        snprintf(k, sizeof k, "bps%d", st);
+        out[k] = best_bps;
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     drop_graph(p);
     return e == cudaSuccess ? GBFFT_OK : cuda_fail(e);
+}
+
+}  // namespace
+
+extern "C" {
+
+int fft_plan_autotune(gbfft_plan_t p, const void *args, gbfft_stream_t stream) {
+    if (!p) return GBFFT_ERR_NULL;
+    int rc = check_plan_ready(p);
+    if (rc) return rc;
+    if (p->kind == KIND_SLAB) return GBFFT_OK;  // its column pass is tuned through a one-image 2D plan
+    if (!args) return GBFFT_ERR_NULL;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    if (p->kind != KIND_BATCH) {
+        const gbfft_tune_args *a = static_cast<const gbfft_tune_args *>(args);
+        if (!a->in || !a->out || (p->kind == KIND_2D && !a->H)) return GBFFT_ERR_NULL;
+        if (misaligned(a->in) || misaligned(a->out) || (p->kind == KIND_2D && misaligned(a->H)))
+            return GBFFT_ERR_MISALIGNED;
+    }
+    const std::string path = tune_cache_path();
+    const std::string key = tune_device_key() + "|" + plan_signature(p);
+    TuneCache cache;
+    tune_cache_load(path, cache);
+    auto hit = cache.find(key);
+    if (hit != cache.end() && apply_tuned(p, hit->second)) return GBFFT_OK;
+    TuneEntry e;
+    if (p->kind == KIND_BATCH)
+        rc = tune_batched(p, static_cast<const gbfft_image_ptrs *>(args), s, e);
+    else if (p->kind == KIND_2D)
+        rc = tune_2d(p, static_cast<const gbfft_tune_args *>(args), s, e);
+    else
+        rc = tune_1d(p, static_cast<const gbfft_tune_args *>(args), s, e);
+    if (rc) return rc;
+    if (!path.empty()) {
+        tune_cache_load(path, cache);  // entries other processes stored meanwhile
+        cache[key] = e;
+        tune_cache_store(path, cache);  // a cache that cannot be written costs a re-tune, nothing else
+    }
+    return GBFFT_OK;
 }
 
 int fft_plan_get_option(gbfft_plan_t p, int key, int64_t *value) {
