@@ -558,9 +558,10 @@ def variant_batched(count: int = 512, steps: int = 5, autotune: bool = True):
 
 def variant_precision(img, H, ref, flush, steps: int = 100):
     """The headline 4096^2 workload with each arithmetic of the radix-16
-    passes: FP32 butterflies, and split-BF16 tensor-core products with 2 and 3
-    BF16 parts; median time over flushed steps and rel-L2 against the FP64
-    oracle output of the same image (`ref`)."""
+    passes: FP32 butterflies; split-BF16 products with 2 and 3 BF16 parts on
+    the warp-level MMA and on tcgen05; TF32 in 2 parts on tcgen05.  Median
+    time over flushed steps and rel-L2 against the FP64 oracle output of the
+    same image (`ref`)."""
     import torch
 
     import paper_cs_0103001_gb300 as gb
@@ -568,7 +569,8 @@ def variant_precision(img, H, ref, flush, steps: int = 100):
 
     res = {}
     out = torch.empty_like(img)
-    for name, prec in (("fp32", 0), ("split_bf16x2", 1), ("split_bf16x3", 2)):
+    for name, prec in (("fp32", 0), ("split_bf16x2", 1), ("split_bf16x3", 2), ("tcgen05_bf16x2", 3),
+                       ("tcgen05_bf16x3", 4), ("tcgen05_tf32x2", 5)):
         plan = gb.Plan2D(img.shape[0], img.shape[1], 1, img.device, {nat.OPT_PRECISION: prec})
         ms = _timed(lambda: plan.filter(img, H, out=out), steps, 5, flush)
         got = out.cpu().numpy().astype(np.float64)
@@ -790,8 +792,9 @@ def main():
     ap.add_argument("--count", type=int, default=512, help="--workload batched: number of images")
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="--workload batched: launch shapes as planned, no tuning launches")
-    ap.add_argument("--precision", type=int, default=2, choices=[1, 2],
-                    help="--workload pipeline4096_tc: 1 = split BF16 x2 (3 products), 2 = x3 (6 products)")
+    ap.add_argument("--precision", type=int, default=4, choices=[1, 2, 3, 4, 5],
+                    help="--workload pipeline4096_tc: mma.sync 1 = split BF16 x2 (3 products), 2 = x3 (6 products); "
+                         "tcgen05 3 = BF16 x2, 4 = BF16 x3, 5 = TF32 x2")
     ap.add_argument("--log2n", type=int, default=20)
     ap.add_argument("--dtype", default="c64", choices=["c64", "c128"])
     ap.add_argument("--onchip", type=int, default=1, choices=[0, 1, 2],

@@ -82,9 +82,13 @@ typedef enum {
      * fft_plan_workspace_bytes (one prepared filter per image in a chunk). */
     GBFFT_OPT_H_BATCH_STRIDE = 2,
     /* Arithmetic of the 2D pipeline's radix-16 passes: 0 = FP32 butterflies
-     * (default); 1 = tensor cores, each operand split into 2 BF16 parts, 3
-     * products (about 16 significant bits per pass); 2 = 3 BF16 parts, 6
-     * products (about 24 bits).  Nonzero values need a 2D plan with sides
+     * (default); tensor cores with each operand split into narrower parts
+     * and FP32 accumulation, on the warp-level MMA (mma.sync): 1 = 2 BF16
+     * parts, 3 products (about 16 significant bits per pass), 2 = 3 BF16
+     * parts, 6 products (about 24 bits); on the fifth-generation tensor
+     * cores (tcgen05.mma, accumulators in tensor memory): 3 = 2 BF16 parts
+     * (3 products), 4 = 3 BF16 parts (6 products), 5 = 2 TF32 parts (3
+     * products, about 22 bits).  Nonzero values need a 2D plan with sides
      * 512..4096 (else GBFFT_ERR_UNSUPPORTED); the filter gradient of the
      * adjoint is always computed with FP32 butterflies. */
     GBFFT_OPT_PRECISION = 3,

@@ -419,7 +419,7 @@ int fft_plan_set_option(gbfft_plan_t p, int key, int64_t value) {
             layout(p);
             return GBFFT_OK;
         case GBFFT_OPT_PRECISION:
-            if (value < 0 || value > 2) return GBFFT_ERR_INVALID_VALUE;
+            if (value < 0 || value > 5) return GBFFT_ERR_INVALID_VALUE;
             if (value != 0 && !(p->kind == KIND_2D && tc_supported(1 << p->log2r, 1 << p->log2c)))
                 return GBFFT_ERR_UNSUPPORTED;
             p->opt_precision = value;
@@ -544,8 +544,12 @@ static int pipeline_chunk(gbfft_plan *p, const float *img, const float *H, float
     float *beta = reinterpret_cast<float *>(p->ws + p->off_beta);
     const float scale = (float)(1.0 / ((double)rows * cols));
     const void *tw = p->ws + p->off_tw0;
-    const int terms = p->opt_precision ? (int)p->opt_precision + 1 : 0;  // split-BF16 tensor-core passes
-    if (!terms && !cropped && p->opt_onchip && onchip_supported(rows, cols)) {
+    // tensor-core radix-16 passes: warp-level split BF16 with `terms` parts
+    // (precision 1, 2), or tcgen05 with format tc5 (precision 3, 4, 5)
+    const int terms = (p->opt_precision == 1 || p->opt_precision == 2) ? (int)p->opt_precision + 1 : 0;
+    const int tc5 = p->opt_precision >= 3 ? (int)p->opt_precision - 3 : -1;
+    int *status = reinterpret_cast<int *>(p->ws + p->off_status);
+    if (!terms && tc5 < 0 && !cropped && p->opt_onchip && onchip_supported(rows, cols)) {
         return launch(p, GBFFT_STAGE_ONCHIP, s, [&] {
             return launch_onchip(img, H, out, p->opt_h_stride, rows, cols, nb, p->ws + p->off_tw0,
                                  p->ws + p->off_tw1, s);
@@ -577,6 +581,7 @@ static int pipeline_chunk(gbfft_plan *p, const float *img, const float *H, float
     }
     rc = launch(p, GBFFT_STAGE_ROWS_FWD, s, [&] {
         if (cropped) return launch_rows_pad(true, img, spec, rows, cols, nb, crop_r, crop_c, tw, s);
+        if (tc5 >= 0) return launch_rows_tc5(true, img, spec, rows, cols, nb, tw, tc5, status, s);
         return terms ? launch_rows_tc(true, img, spec, rows, cols, nb, tw, terms, s)
                      : launch_rows_fwd(img, spec, rows, cols, nb, tw, s);
     });
@@ -587,6 +592,9 @@ static int pipeline_chunk(gbfft_plan *p, const float *img, const float *H, float
     }
     const long long hs_img = per_image ? half_px : 0, beta_img = per_image ? rows : 0;
     rc = launch(p, GBFFT_STAGE_COLS, s, [&] {
+        if (tc5 >= 0)
+            return launch_cols_tc5(spec, hs, beta, hs_img, beta_img, rows, cols, nb, p->ws + p->off_tw1, tc5, status,
+                                   s);
         return terms ? launch_cols_tc(spec, hs, beta, hs_img, beta_img, rows, cols, nb, p->ws + p->off_tw1, terms, s)
                      : launch_cols_filter(spec, hs, beta, hs_img, beta_img, rows, cols, nb, p->ws + p->off_tw1,
                                           reinterpret_cast<int *>(p->ws + p->off_status), s, ColSlab{0, 0, 0},
@@ -595,6 +603,7 @@ static int pipeline_chunk(gbfft_plan *p, const float *img, const float *H, float
     if (rc) return rc;
     return launch(p, GBFFT_STAGE_ROWS_INV, s, [&] {
         if (cropped) return launch_rows_pad(false, spec, out, rows, cols, nb, crop_r, crop_c, tw, s);
+        if (tc5 >= 0) return launch_rows_tc5(false, spec, out, rows, cols, nb, tw, tc5, status, s);
         return terms ? launch_rows_tc(false, spec, out, rows, cols, nb, tw, terms, s)
                      : launch_rows_inv(spec, out, rows, cols, nb, tw, reinterpret_cast<int *>(p->ws + p->off_status), s);
     });

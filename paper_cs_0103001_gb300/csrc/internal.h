@@ -112,6 +112,13 @@ cudaError_t launch_rows_tc(bool fwd, const void *src, void *dst, int rows, int c
                            int terms, cudaStream_t s);
 cudaError_t launch_cols_tc(void *spec, const float *hs, const float *beta, long long hs_img, long long beta_img,
                            int rows, int cols, int nimg, const void *tw_rows, int terms, cudaStream_t s);
+// Fifth-generation tensor-core variants (tc5_2d.cu, tcgen05.mma): fmt 0 =
+// BF16 x 2 parts (3 products), 1 = BF16 x 3 (6 products), 2 = TF32 x 2 (3
+// products); sides 512..4096; a bounded MMA wait that gives up sets *status.
+cudaError_t launch_rows_tc5(bool fwd, const void *src, void *dst, int rows, int cols, int nimg, const void *tw,
+                            int fmt, int *status, cudaStream_t s);
+cudaError_t launch_cols_tc5(void *spec, const float *hs, const float *beta, long long hs_img, long long beta_img,
+                            int rows, int cols, int nimg, const void *tw_rows, int fmt, int *status, cudaStream_t s);
 // Adjoint column pass (cols_grad.cu): per column, loop over nimg images of
 // spec_x / spec_g, accumulate scale * sum Re(conj(W G) W x) into grad_T
 // [cols/2 + 1][rows] (slot order; added to its contents when `accumulate`),

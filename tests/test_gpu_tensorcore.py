@@ -1,5 +1,7 @@
-"""The 2D pipeline with its radix-16 passes as split-BF16 DFT-matrix products
-on the tensor cores (GBFFT_OPT_PRECISION 1 and 2), against the FP64 oracle.
+"""The 2D pipeline with its radix-16 passes as split-precision DFT-matrix
+products on the tensor cores, against the FP64 oracle: warp-level mma.sync
+(GBFFT_OPT_PRECISION 1 and 2) and the fifth-generation tcgen05.mma with
+accumulators in tensor memory (3, 4: BF16 in 2 or 3 parts; 5: TF32 in 2).
 
 Two BF16 parts per operand (three products) keep about 16 significant bits
 per pass, so that variant is held to a looser bound than FP32 and its error
@@ -38,6 +40,21 @@ def test_split_bf16_pipeline(rows, cols):
     assert e3 <= tol_fp32(rows * cols)
     assert e2 <= 50 * tol_fp32(rows * cols)
     assert e3 <= e2
+
+
+@pytest.mark.parametrize("rows,cols", [(512, 512), (1024, 512), (512, 2048), (2048, 1024), (4096, 4096)])
+def test_tcgen05_pipeline(rows, cols):
+    """tcgen05 passes: six BF16 products and three TF32 products meet the FP32
+    tolerance; three BF16 products keep about 16 bits per pass, as on mma.sync."""
+    e32 = _run(rows, cols, 0, 51)
+    e3 = _run(rows, cols, 3, 51)
+    e4 = _run(rows, cols, 4, 51)
+    e5 = _run(rows, cols, 5, 51)
+    print(f"{rows}x{cols}: fp32 {e32:.2e}  tcgen05 bf16x2 {e3:.2e}  bf16x3 {e4:.2e}  tf32x2 {e5:.2e}")
+    assert e4 <= tol_fp32(rows * cols)
+    assert e5 <= tol_fp32(rows * cols)
+    assert e3 <= 50 * tol_fp32(rows * cols)
+    assert e4 <= e3
 
 
 def test_unsupported_sizes_are_refused():
