@@ -21,12 +21,14 @@
 // fft_core.cuh): FP32 twiddles; every thread splits its row and stores it
 // into its group's A tiles (128 butterflies per group, no-swizzle K-major
 // layout: 8-row x 16-byte core matrices, K groups LBO = 128 bytes apart, row
-// groups SBO apart); one thread issues the MMAs and commits them to an
-// mbarrier; every thread waits (bounded), loads its row of D from tensor
-// memory (its warp's lane quarter), and the outputs go to their Stockham
-// destinations through the FP32 exchange buffer.  The A tiles overlay the
-// exchange buffers: A is written after the previous exchange was read (block
-// barrier) and the exchange is written after the MMAs that read A completed.
+// groups SBO apart); the group (four warps) meets at its own named barrier,
+// its first thread issues the group's MMAs and commits them to the group's
+// mbarrier; the group's threads wait (bounded), load their rows of D from
+// tensor memory (each warp its lane quarter), and the outputs go to their
+// Stockham destinations through the FP32 exchange buffer.  Groups run
+// independently up to the exchange, so one group's MMAs overlap another's
+// staging.  The A tiles have shared memory of their own: a group rewrites its
+// tiles only after its previous MMAs completed.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -75,21 +77,41 @@ struct Tc5State {
     uint32_t tmem;   // tensor-memory base; group g's accumulator at column 32 g
     uint32_t a_sh;   // shared address of the A tiles [part][group]
     uint32_t b_sh;   // shared address of the DFT matrices [direction][part]
-    uint32_t bar;    // shared address of the MMA-completion mbarrier
+    uint32_t bar;    // shared address of this thread's group's MMA-completion mbarrier
     uint64_t *barp;  // the same mbarrier
-    uint32_t phase;  // MMA batches completed so far
+    uint32_t phase;  // MMA batches of this group completed so far
     int ngroups;     // butterflies per pass / 128
     int *status;     // device status word for a wait that gave up (may be null)
 };
 
+// Waits for one batch of MMAs (each try suspends for a hardware time limit of
+// microseconds at most); far more than a batch takes.
+constexpr uint32_t kTc5Tries = 1u << 16;
+
+// Bounded wait for phase `parity` of an mbarrier: mbarrier.try_wait suspends
+// the thread in hardware until the phase completes or a time limit passes;
+// at most `tries` such waits.
+__device__ __forceinline__ bool mbar_try_wait_bounded(uint64_t *bar, uint32_t parity, uint32_t tries) {
+    const uint32_t a = smem_u32(bar);
+    for (uint32_t i = 0; i < tries; ++i) {
+        uint32_t done;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
 template <int FMT> struct Tc5Layout {
     typedef Tc5Fmt<FMT> F;
-    // bytes of shared memory the policy needs beside the body's own: the A
-    // tiles (which may overlay the body's exchange buffers) are counted by
-    // a_bytes(); the DFT matrices, mbarrier and TMEM slot follow them
+    // shared memory the policy needs beside the body's own: the A tiles, then
+    // the DFT matrices, one mbarrier per group and the TMEM slot
     static constexpr size_t a_bytes(int threads) { return (size_t)F::TERMS * (threads / 128) * F::TILE; }
     static constexpr size_t b_bytes() { return (size_t)2 * F::TERMS * F::BTILE; }
-    static constexpr size_t tail_bytes() { return b_bytes() + 64; }
+    static constexpr size_t bytes(int threads) { return a_bytes(threads) + b_bytes() + 8 * 8 + 16; }
 };
 
 // TMEM columns for `groups` accumulators of 32 columns (a power of two >= 32)
@@ -98,15 +120,15 @@ __host__ __device__ constexpr int tc5_cols(int groups) {
 }
 
 // Set up at kernel start (every thread of the block): DFT matrices into
-// shared memory, the mbarrier, tensor memory.  `a` = the A-tile area,
-// `tail` = Tc5Layout::tail_bytes() of shared memory outside it.
+// shared memory, the mbarriers, tensor memory.  `a` = Tc5Layout::bytes(blockDim.x)
+// of shared memory (128-byte aligned) of the policy's own.
 template <int FMT>
-__device__ __forceinline__ void tc5_setup(Tc5State &st, unsigned char *a, unsigned char *tail, int *status) {
+__device__ __forceinline__ void tc5_setup(Tc5State &st, unsigned char *a, int *status) {
     typedef Tc5Fmt<FMT> F;
-    unsigned char *b = tail;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(tail + Tc5Layout<FMT>::b_bytes());
-    uint32_t *slot = reinterpret_cast<uint32_t *>(tail + Tc5Layout<FMT>::b_bytes() + 8);
     const int groups = blockDim.x / 128;
+    unsigned char *b = a + Tc5Layout<FMT>::a_bytes(blockDim.x);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(b + Tc5Layout<FMT>::b_bytes());
+    uint32_t *slot = reinterpret_cast<uint32_t *>(bars + 8);
     // B[n][k] for direction d (0: forward, DIR = -1; 1: inverse, DIR = +1):
     // n < 16: Re y_n = sum_k C x_re - S x_im;  n >= 16: Im y_(n-16) = S x_re + C x_im
     // cos and sin of 2 pi m / 16 from the exact constants of the 16-point
@@ -149,7 +171,7 @@ __device__ __forceinline__ void tc5_setup(Tc5State &st, unsigned char *a, unsign
                      : "memory");
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
     }
-    if (threadIdx.x == 0) mbar_init(bar, 1);
+    if (threadIdx.x < groups) mbar_init(&bars[threadIdx.x], 1);
     fence_async_smem();
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
     __syncthreads();
@@ -157,8 +179,8 @@ __device__ __forceinline__ void tc5_setup(Tc5State &st, unsigned char *a, unsign
     st.tmem = *slot;
     st.a_sh = smem_u32(a);
     st.b_sh = smem_u32(b);
-    st.bar = smem_u32(bar);
-    st.barp = bar;
+    st.bar = smem_u32(&bars[threadIdx.x >> 7]);
+    st.barp = &bars[threadIdx.x >> 7];
     st.phase = 0;
     st.ngroups = groups;
     st.status = status;
@@ -236,12 +258,12 @@ __device__ __forceinline__ void tc5_store_row(const Tc5State &st, const float2 (
     }
 }
 
-// One thread: the MMAs of every group, committed to the mbarrier.
+// One thread of group g: the group's MMAs, committed to the group's mbarrier.
 template <int FMT, int DIR>
-__device__ __forceinline__ void tc5_issue(const Tc5State &st) {
+__device__ __forceinline__ void tc5_issue(const Tc5State &st, int g) {
     typedef Tc5Fmt<FMT> F;
     const int d = DIR < 0 ? 0 : 1;
-    for (int g = 0; g < st.ngroups; ++g) {
+    {
         const uint32_t dt = st.tmem + 32u * g;
         int first = 1;
 #pragma unroll
@@ -300,16 +322,15 @@ __device__ __forceinline__ void tc5_pass16(float2 (&v)[16], float2 *sm, const fl
         }
     }
     const int row = threadIdx.x, g = row >> 7, m = row & 127;
-    __syncthreads();  // the previous exchange's reads (and the caller's staging reads) are complete
-    tc5_store_row<FMT>(st, v, g, m);
+    tc5_store_row<FMT>(st, v, g, m);  // the group's previous MMAs completed: its tiles are free
     fence_async_smem();
     asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
-    __syncthreads();
-    if (threadIdx.x == 0) {
+    asm volatile("bar.sync %0, 128;\n" ::"r"(1 + g) : "memory");  // the group's rows are stored
+    if (m == 0) {
         asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
-        tc5_issue<FMT, DIR>(st);
+        tc5_issue<FMT, DIR>(st, g);
     }
-    const bool ok = mbar_wait_bounded(st.barp, st.phase & 1, kTmaPolls);
+    const bool ok = mbar_try_wait_bounded(st.barp, st.phase & 1, kTc5Tries);
     ++st.phase;
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     if (!ok) {

@@ -5,7 +5,7 @@
 // the transform policy Tc5Fft<FMT> (fft_tc5.cuh).  Each kernel sets the
 // policy up at its start (the DFT matrices in shared memory, an mbarrier, 32
 // tensor-memory columns per 128 threads) and releases the tensor memory at
-// its end; the A tiles overlay the body's own shared memory.  Sides
+// its end; its shared memory follows the body's own.  Sides
 // 512..4096, as the warp-level tensor-core variant (tc2d.cu).
 #include "cols_impl.cuh"
 #include "fft_tc5.cuh"
@@ -16,11 +16,9 @@ namespace gbfft {
 
 template <int THREADS, int FMT> struct Tc5Smem {
     static constexpr size_t align128(size_t x) { return (x + 127) / 128 * 128; }
-    // the A tiles overlay the body's shared memory; the rest follows both
-    static constexpr size_t area(size_t body) {
-        return align128(body > Tc5Layout<FMT>::a_bytes(THREADS) ? body : Tc5Layout<FMT>::a_bytes(THREADS));
-    }
-    static constexpr size_t total(size_t body) { return area(body) + Tc5Layout<FMT>::tail_bytes(); }
+    // the body's shared memory, then the policy's own
+    static constexpr size_t area(size_t body) { return align128(body); }
+    static constexpr size_t total(size_t body) { return area(body) + Tc5Layout<FMT>::bytes(THREADS); }
 };
 
 template <int M, int FMT>
@@ -31,7 +29,7 @@ __global__ void __launch_bounds__(RowCfg<M>::THREADS, 1)
     typedef Tc5Smem<RowCfg<M>::THREADS, FMT> S;
     const size_t y = blockIdx.y;
     Tc5Fft<FMT> f;
-    tc5_setup<FMT>(f.st, smraw, smraw + S::area(RowCfg<M>::SMEM), status);
+    tc5_setup<FMT>(f.st, smraw + S::area(RowCfg<M>::SMEM), status);
     rows_fwd_body<M, Tc5Fft<FMT>>(img + y * N * M, spec + y * (M / 2) * N, N, log2g, tw, blockIdx.x, smraw, f);
     tc5_teardown(f.st);
 }
@@ -44,7 +42,7 @@ __global__ void __launch_bounds__(RowCfg<M>::THREADS, 1)
     typedef Tc5Smem<RowCfg<M>::THREADS, FMT> S;
     const size_t y = blockIdx.y;
     Tc5Fft<FMT> f;
-    tc5_setup<FMT>(f.st, smraw, smraw + S::area(RowCfg<M>::SMEM), status);
+    tc5_setup<FMT>(f.st, smraw + S::area(RowCfg<M>::SMEM), status);
     rows_inv_body<M, Tc5Fft<FMT>>(spec + y * (M / 2) * N, out + y * N * M, N, log2g, tw, blockIdx.x, smraw, f);
     tc5_teardown(f.st);
 }
@@ -57,7 +55,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, 2)
     typedef Tc5Smem<ColCfg<N>::THREADS, FMT> S;
     const size_t y = blockIdx.y;
     Tc5Fft<FMT> f;
-    tc5_setup<FMT>(f.st, smraw, smraw + S::area(ColCfg<N>::SMEM), status);
+    tc5_setup<FMT>(f.st, smraw + S::area(ColCfg<N>::SMEM), status);
     cols_body<N, Tc5Fft<FMT>>(spec + y * (M / 2) * N, PreparedFilter{hs + y * hs_img, beta + y * beta_img, N}, M,
                               log2g, tw, blockIdx.x, smraw, f);
     tc5_teardown(f.st);
