@@ -227,7 +227,7 @@ def run_gbfft(args):
     plan = gb.Plan2D(ROWS, COLS, 1, dev)
     # the library's autotuner picks the plan's configuration (cached per GPU
     # and shape, so only the first run on a machine times the candidates)
-    tuning = plan.autotune(img, H, out)
+    tuning = plan.autotune(img, H, out) if args.tune else "not tuned (--no-tune): the plan's defaults"
     stream = torch.cuda.current_stream(dev)
 
     def step():
@@ -801,6 +801,8 @@ def main():
                     help="--workload fft1d: the plan's on-chip option (2 = cluster path at 2^15..2^17)")
     ap.add_argument("--no-variants", dest="variants", action="store_false",
                     help="headline only, without the other workloads")
+    ap.add_argument("--no-tune", dest="tune", action="store_false",
+                    help="headline plan with its default configuration (no autotuner launches, e.g. under ncu)")
     args = ap.parse_args()
     if args.impl == "gbfft" and args.workload != "pipeline4096":
         print(json.dumps(run_workload(args)), flush=True)
