@@ -383,6 +383,25 @@ int gbfft_plan_profile_read(gbfft_plan_t plan, double *ms, int64_t *launches, in
  * records it here: GBFFT_ERR_TIMEOUT.  GBFFT_OK otherwise. */
 int gbfft_device_status(gbfft_plan_t plan);
 
+/* Guard bands (a stand-in for a memory checker, in every build): the plan's
+ * workspace holds 256 bytes of a fixed pattern before, between and after its
+ * regions (twiddle tables, prepared filters, spectra, work lists, ...),
+ * written when the workspace is bound.  This call waits for the device
+ * (cudaDeviceSynchronize), checks every band and writes the number of 4-byte
+ * words found changed to *bad_words (0: no kernel wrote outside its region
+ * into a band).  GBFFT_ERR_WORKSPACE if no workspace is bound. */
+int gbfft_plan_check_guards(gbfft_plan_t plan, int64_t *bad_words);
+
+/* Index-bound checks (a stand-in for a memory checker): in the library built
+ * with GBFFT_CHECKED (libgbfft_checked.so), the kernels check the index
+ * arithmetic of their pair and slot runs, tensor-map boxes, work-list items
+ * and tensor-memory columns; a failing check records its site code (see
+ * check.cuh) and the access is skipped (no trap).  This call waits for the
+ * device, then writes the first failing site (0 = none) and the number of
+ * failures since the last call, and clears them.  GBFFT_ERR_UNSUPPORTED in
+ * the normal build. */
+int gbfft_checked_take(int64_t *first_site, int64_t *failures);
+
 /* Diagnostic of that path: launches on `stream` one block that waits on an
  * mbarrier no copy will ever complete, testing it at most `polls` times
  * (1 .. 2^22, each test followed by a 64 ns sleep); the wait gives up, records

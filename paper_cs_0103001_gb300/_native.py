@@ -11,7 +11,9 @@ import ctypes
 import os
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_PKG, "libgbfft.so")
+# GBFFT_CHECKED=1 loads the index-checking build (built by build.build(checked=True))
+CHECKED = os.environ.get("GBFFT_CHECKED", "") not in ("", "0")
+LIB_PATH = os.path.join(_PKG, "libgbfft_checked.so" if CHECKED else "libgbfft.so")
 
 # gbfft_dtype
 C64 = 1
@@ -67,6 +69,8 @@ SIGNATURES = {
     "fft2_spectrum": (_INT, [_P, _P, _I64, _I64, _P, _P]),
     "fft2_filter_ifft2_analytic": (_INT, [_P, _P, _INT, ctypes.c_double, ctypes.c_double, _P, _P]),
     "gbfft_device_status": (_INT, [_P]),
+    "gbfft_plan_check_guards": (_INT, [_P, ctypes.POINTER(ctypes.c_int64)]),
+    "gbfft_checked_take": (_INT, [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "gbfft_selftest_wait_timeout": (_INT, [_P, _I64, _P]),
     "fft2_filter_ifft2_backward": (_INT, [_P, _P, _P, _P, _P, _P, _P]),
     "fft_plan_destroy": (_INT, [_P]),
@@ -100,7 +104,8 @@ def _load() -> ctypes.CDLL:
     if not os.path.exists(LIB_PATH):
         raise RuntimeError(
             f"libgbfft.so not found at {LIB_PATH}: build it first "
-            "(python -c 'import __graft_entry__ as g; g.build()')"
+            "(python -c 'import __graft_entry__ as g; g.build()'; the checked build: "
+            "paper_cs_0103001_gb300.build.build(checked=True))"
         )
     so = ctypes.CDLL(LIB_PATH)
     for name, (res, args) in SIGNATURES.items():

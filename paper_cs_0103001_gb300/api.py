@@ -80,6 +80,12 @@ class _PlanBase:
         nat.call("fft_plan_get_option", self.handle, int(key), ctypes.byref(v))
         return int(v.value)
 
+    def check_guards(self) -> int:
+        """Words changed in the workspace's guard bands (0 = none; synchronous)."""
+        n = ctypes.c_int64()
+        nat.call("gbfft_plan_check_guards", self.handle, ctypes.byref(n))
+        return int(n.value)
+
     def _autotune(self, x: torch.Tensor, H: torch.Tensor | None, out: torch.Tensor) -> None:
         args = _TuneArgs(_P(x.data_ptr()), _P(H.data_ptr()) if H is not None else _P(), _P(out.data_ptr()))
         with self.lock:

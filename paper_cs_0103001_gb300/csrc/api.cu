@@ -12,6 +12,7 @@
 #include <string>
 
 #include "batched.h"
+#include "check.cuh"
 #include "gbfft.h"
 #include "internal.h"
 #include "tma.cuh"
@@ -62,6 +63,11 @@ struct gbfft_plan {
     int nranks = 1, rank = 0;    // slab plans: the decomposition and this rank
     int fs_l1 = 0, fs_l2 = 0;    // four-step split
     std::vector<ProfRec> prof;
+    // guard bands: kAlign bytes of a fixed pattern after every workspace
+    // region (offsets here, and as a table in the workspace for the kernels
+    // that fill and check them)
+    std::vector<long long> guards;
+    size_t off_guards = 0;
     // batched plans (KIND_BATCH)
     std::vector<BatchImage> bimgs;
     std::vector<BatchItem> bitems[kBatchStages];
@@ -90,20 +96,41 @@ size_t csize(const gbfft_plan *p) { return is_dbl(p) ? 16 : 8; }
 
 int max_single_log2(const gbfft_plan *p) { return is_dbl(p) ? kMaxSinglePassLog2F64 : kMaxSinglePassLog2F32; }
 
+// End of a workspace region at `end`: the guard band after it, and where the
+// next region starts.
+size_t region_end(gbfft_plan *p, size_t end) {
+    const size_t g = align_up(end);
+    p->guards.push_back((long long)g);
+    return g + kAlign;
+}
+
+// The guard table (one offset per guard, the table's own guard included)
+// and the status words close the layout.
+void layout_close(gbfft_plan *p, size_t off) {
+    p->off_guards = off;
+    const size_t n = p->guards.size() + 1;  // and the guard after the table itself
+    off = align_up(off + n * sizeof(long long));
+    p->guards.push_back((long long)off);
+    off += kAlign;
+    p->off_status = off;
+    p->need = off + kAlign;
+}
+
 void layout_batched(gbfft_plan *p) {
-    size_t off = 0;
+    size_t off = kAlign;  // a guard band before the first region
+    p->guards.assign(1, 0);
     p->off_bimgs = off;
-    off = align_up(off + p->bimgs.size() * sizeof(BatchImage));
+    off = region_end(p, off + p->bimgs.size() * sizeof(BatchImage));
     for (int st = 0; st < kBatchStages; ++st) {
         p->off_bitems[st] = off;
-        off = align_up(off + p->bitems[st].size() * sizeof(BatchItem));
+        off = region_end(p, off + p->bitems[st].size() * sizeof(BatchItem));
     }
     p->tw_off.clear();
     for (const BatchImage &im : p->bimgs) {
         for (int len : {im.cols, im.rows}) {
             if (p->tw_off.count(len)) continue;
             p->tw_off[len] = off;
-            off = align_up(off + (size_t)len * 8);
+            off = region_end(p, off + (size_t)len * 8);
         }
     }
     for (BatchImage &im : p->bimgs) {
@@ -111,20 +138,19 @@ void layout_batched(gbfft_plan *p) {
         im.twc_off = (long long)p->tw_off[im.cols];
         im.twr_off = (long long)p->tw_off[im.rows];
         im.spec_off = (long long)off;
-        off = align_up(off + half_px * 8);
+        off = region_end(p, off + half_px * 8);
         im.hs_off = (long long)off;
-        off = align_up(off + half_px * 4);
+        off = region_end(p, off + half_px * 4);
         im.beta_off = (long long)off;
-        off = align_up(off + (size_t)im.rows * 4);
+        off = region_end(p, off + (size_t)im.rows * 4);
     }
-    p->off_status = align_up(off);
-    off = p->off_status + kAlign;
-    p->need = off;
+    layout_close(p, off);
 }
 
 // Compute the workspace layout for the current options.
 void layout(gbfft_plan *p) {
-    size_t off = 0;
+    size_t off = kAlign;  // a guard band before the first region
+    p->guards.assign(1, 0);
     if (p->kind == KIND_BATCH) {
         layout_batched(p);
         return;
@@ -133,22 +159,21 @@ void layout(gbfft_plan *p) {
         const int64_t rows = int64_t(1) << p->log2r, cols = int64_t(1) << p->log2c;
         const int64_t mloc = cols / 2 / p->nranks;  // this rank's half-spectrum columns
         p->off_tw0 = off;  // row transforms (length cols)
-        off = align_up(off + (size_t)cols * 8);
+        off = region_end(p, off + (size_t)cols * 8);
         p->off_tw1 = off;  // column transforms (length rows)
-        off = align_up(off + (size_t)rows * 8);
+        off = region_end(p, off + (size_t)rows * 8);
         p->off_hs = off;  // prepared filter of this rank's columns, [mloc][rows]
-        off = align_up(off + (size_t)mloc * rows * 4);
+        off = region_end(p, off + (size_t)mloc * rows * 4);
         p->off_beta = off;
-        off = align_up(off + (size_t)rows * 4);
-        p->off_status = align_up(off);
-        p->need = p->off_status + kAlign;
+        off = region_end(p, off + (size_t)rows * 4);
+        layout_close(p, off);
         return;
     }
     if (p->kind == KIND_1D) {
         const int64_t n = int64_t(1) << p->log2n;
         if (p->log2n <= max_single_log2(p)) {
             p->off_tw0 = off;
-            off = align_up(off + (size_t)n * csize(p));
+            off = region_end(p, off + (size_t)n * csize(p));
             p->off_tw1 = p->off_tw2 = p->off_buf = off;
             p->chunk = p->batch;
         } else {
@@ -157,15 +182,15 @@ void layout(gbfft_plan *p) {
             const int lf = (p->log2n + 1) / 2;
             const int64_t n4s = (int64_t(1) << lf) + (n >> lf);
             p->off_tw0 = off;
-            off = align_up(off + (size_t)n1 * csize(p));
+            off = region_end(p, off + (size_t)n1 * csize(p));
             p->off_tw1 = off;
-            off = align_up(off + (size_t)n2 * csize(p));
+            off = region_end(p, off + (size_t)n2 * csize(p));
             p->off_tw2 = off;
-            off = align_up(off + (size_t)n4s * csize(p));
+            off = region_end(p, off + (size_t)n4s * csize(p));
             p->off_tw5 = off;  // coarse inter-pass table of pass A
-            off = align_up(off + (size_t)16 * n2 * csize(p));
+            off = region_end(p, off + (size_t)16 * n2 * csize(p));
             p->off_tw3 = off;  // full inter-pass table of the cluster path
-            if (fft1d_cluster_supported(p->log2n, is_dbl(p))) off = align_up(off + (size_t)n * csize(p));
+            if (fft1d_cluster_supported(p->log2n, is_dbl(p))) off = region_end(p, off + (size_t)n * csize(p));
             p->off_buf = off;
             int64_t chunk = p->opt_chunk;
             if (chunk <= 0) {
@@ -176,14 +201,14 @@ void layout(gbfft_plan *p) {
             }
             if (chunk > p->batch) chunk = p->batch;
             p->chunk = chunk;
-            off = align_up(off + (size_t)chunk * n * csize(p));
+            off = region_end(p, off + (size_t)chunk * n * csize(p));
         }
     } else {
         const int64_t rows = int64_t(1) << p->log2r, cols = int64_t(1) << p->log2c;
         p->off_tw0 = off;  // row transforms (length cols)
-        off = align_up(off + (size_t)cols * 8);
+        off = region_end(p, off + (size_t)cols * 8);
         p->off_tw1 = off;  // column transforms (length rows)
-        off = align_up(off + (size_t)rows * 8);
+        off = region_end(p, off + (size_t)rows * 8);
         p->off_tw2 = off;
         const int64_t half_px = rows * (cols / 2);
         const int64_t img_bytes = half_px * 8;
@@ -199,22 +224,20 @@ void layout(gbfft_plan *p) {
         p->chunk = chunk;
         const int64_t nfilt = p->opt_h_stride != 0 ? chunk : 1;  // prepared filters held at once
         p->off_hs = off;
-        off = align_up(off + (size_t)nfilt * half_px * 4);
+        off = region_end(p, off + (size_t)nfilt * half_px * 4);
         p->off_beta = off;
-        off = align_up(off + (size_t)nfilt * rows * 4);
+        off = region_end(p, off + (size_t)nfilt * rows * 4);
         p->off_buf = off;
-        off = align_up(off + (size_t)chunk * img_bytes);
+        off = region_end(p, off + (size_t)chunk * img_bytes);
         p->off_buf2 = off;  // G's spectra and the filter-gradient sums (adjoint only)
         p->off_grad = off;
         if (p->opt_backward) {
-            off = align_up(off + (size_t)chunk * img_bytes);
+            off = region_end(p, off + (size_t)chunk * img_bytes);
             p->off_grad = off;
-            off = align_up(off + (size_t)(cols / 2 + 1) * rows * 4);
+            off = region_end(p, off + (size_t)(cols / 2 + 1) * rows * 4);
         }
     }
-    p->off_status = align_up(off);
-    off = p->off_status + kAlign;
-    p->need = off;
+    layout_close(p, off);
 }
 
 int cuda_fail(cudaError_t e) {
@@ -477,7 +500,15 @@ int fft_plan_bind_workspace(gbfft_plan_t p, void *workspace, size_t bytes, gbfft
     const bool dbl = is_dbl(p);
     int rc;
     {
-        cudaError_t e = cudaMemsetAsync(p->ws + p->off_status, 0, sizeof(int), s);
+        // status words, then the guard table (from the plan's host copy, which
+        // outlives the copy) and the guard bands
+        cudaError_t e = cudaMemsetAsync(p->ws + p->off_status, 0, 2 * sizeof(int), s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(p->ws + p->off_guards, p->guards.data(), p->guards.size() * sizeof(long long),
+                                cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+            e = launch_guard_fill(p->ws, reinterpret_cast<const long long *>(p->ws + p->off_guards),
+                                  (int)p->guards.size(), (long long)p->ws_bytes, s);
         if (e != cudaSuccess) return cuda_fail(e);
     }
     if (p->kind == KIND_1D) {
@@ -1258,6 +1289,41 @@ int gbfft_device_status(gbfft_plan_t p) {
     if (e == cudaSuccess && word != 0) e = cudaMemset(p->ws + p->off_status, 0, sizeof(int));
     if (e != cudaSuccess) return cuda_fail(e);
     return word ? GBFFT_ERR_TIMEOUT : GBFFT_OK;
+}
+
+int gbfft_plan_check_guards(gbfft_plan_t p, int64_t *bad_words) {
+    int rc = check_plan_ready(p);
+    if (rc) return rc;
+    if (!bad_words) return GBFFT_ERR_NULL;
+    // wait for the plan's work on every stream, then check on the legacy stream
+    cudaError_t e = cudaDeviceSynchronize();
+    unsigned *bad = reinterpret_cast<unsigned *>(p->ws + p->off_status + sizeof(int));
+    if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(unsigned), 0);
+    if (e == cudaSuccess)
+        e = launch_guard_check(p->ws, reinterpret_cast<const long long *>(p->ws + p->off_guards),
+                               (int)p->guards.size(), (long long)p->ws_bytes, bad, 0);
+    unsigned n = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&n, bad, sizeof n, cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e);
+    *bad_words = (int64_t)n;
+    return GBFFT_OK;
+}
+
+int gbfft_checked_take(int64_t *first_site, int64_t *failures) {
+    if (!first_site || !failures) return GBFFT_ERR_NULL;
+    *first_site = 0;
+    *failures = 0;
+    if (!kChecked) return GBFFT_ERR_UNSUPPORTED;
+    cudaError_t e = cudaDeviceSynchronize();
+    cudaError_t (*takes[])(unsigned *) = {check_take_rows, check_take_cols, check_take_batched, check_take_fourstep,
+                                          check_take_tc2d, check_take_tc5};
+    for (auto take : takes) {
+        unsigned w[2] = {0u, 0u};
+        if (e == cudaSuccess) e = take(w);
+        if (!*first_site && w[0]) *first_site = w[0];
+        *failures += w[1];
+    }
+    return e == cudaSuccess ? GBFFT_OK : cuda_fail(e);
 }
 
 int gbfft_selftest_wait_timeout(gbfft_plan_t p, int64_t polls, gbfft_stream_t stream) {

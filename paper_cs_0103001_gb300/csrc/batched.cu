@@ -43,6 +43,9 @@ __device__ __noinline__ void cols_case(const BatchImage &im, char *ws, int bx, u
 
 #define GBFFT_BATCH_SIZES(X) X(4) X(5) X(6) X(7) X(8) X(9) X(10) X(11) X(12)
 
+// columns per block of the column body for `rows`-row columns (ColCfg<N>::W)
+__device__ __forceinline__ int batch_col_w(int rows) { return rows >= 4096 ? 1 : 4096 / rows; }
+
 __global__ void __launch_bounds__(kBatchRowThreads, 2)
     k_batched_rows_fwd(const BatchImage *__restrict__ imgs, const BatchItem *__restrict__ items, int nitems,
                        const gbfft_image_ptrs *__restrict__ ptrs, char *ws) {
@@ -52,6 +55,7 @@ __global__ void __launch_bounds__(kBatchRowThreads, 2)
         const BatchImage im = imgs[it.img];
         const gbfft_image_ptrs pp = ptrs[it.img];
         __syncthreads();  // shared memory of the previous item is free
+        if (!chk(it.bx >= 0 && it.bx < ((im.rows >> 1) >> im.log2g), CK_BATCH_ITEM)) continue;  // uniform
         switch (im.log2c) {
 #define GBFFT_C(L) \
     case L: fwd_case<L>(im, pp, ws, it.bx, smraw); break;
@@ -95,6 +99,7 @@ __global__ void __launch_bounds__(kBatchColThreads, 2)
         const BatchItem it = items[i];
         const BatchImage im = imgs[it.img];
         __syncthreads();
+        if (!chk(it.bx >= 0 && it.bx * batch_col_w(im.rows) < (im.cols >> 1), CK_BATCH_ITEM)) continue;  // uniform
         switch (im.log2r) {
 #define GBFFT_C(L) \
     case L: cols_case<L>(im, ws, it.bx, smraw); break;
@@ -114,6 +119,7 @@ __global__ void __launch_bounds__(kBatchRowThreads, 2)
         const BatchImage im = imgs[it.img];
         const gbfft_image_ptrs pp = ptrs[it.img];
         __syncthreads();
+        if (!chk(it.bx >= 0 && it.bx < ((im.rows >> 1) >> im.log2g), CK_BATCH_ITEM)) continue;  // uniform
         switch (im.log2c) {
 #define GBFFT_C(L) \
     case L: inv_case<L>(im, pp, ws, it.bx, smraw); break;
@@ -125,6 +131,8 @@ __global__ void __launch_bounds__(kBatchRowThreads, 2)
 }
 
 // ---- host side: shapes of the block bodies -------------------------------
+
+cudaError_t check_take_batched(unsigned out[2]) { return check_word_take(out); }
 
 int batch_row_pairs(int cols) {
     switch (ilog2(cols)) {

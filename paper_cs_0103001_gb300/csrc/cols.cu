@@ -149,7 +149,7 @@ __device__ __noinline__ void cols_tma_column(const CUtensorMap *map, float2 *bf,
                                              const float *bt, long long c, bool col0, bool prefetch, int b,
                                              const float2 *__restrict__ tw, int log2g, unsigned char *base,
                                              const float *hs, long long hs_img, int log2half, int crows,
-                                             int boxr, long long cstride, int nchunk) {
+                                             int boxr, long long cstride, int nchunk, long long nrows) {
     typedef ColTmaCfg<N, GF, BL> K;
     constexpr int E = K::E, T = K::T;
     const int t = threadIdx.x;
@@ -174,7 +174,8 @@ __device__ __noinline__ void cols_tma_column(const CUtensorMap *map, float2 *bf,
         mbar_expect_tx(bar, (uint32_t)(N * sizeof(float2) + K::FB));
         for (int q = 0; q < nchunk; ++q)
             for (int r = 0; r < crows; r += boxr)
-                tma_load_2d(nb + (q * crows + r) * 16, map, 0, (int)(q * cstride + cn * crows + r), bar);
+                if (chk(q * cstride + cn * crows + r + boxr <= nrows, CK_COL_BOX))
+                    tma_load_2d(nb + (q * crows + r) * 16, map, 0, (int)(q * cstride + cn * crows + r), bar);
         if constexpr (!GF)
             bulk_load(nf, hs + (cn >> log2half) * hs_img + (cn & ((1LL << log2half) - 1)) * N, N * sizeof(float),
                       bar);
@@ -207,7 +208,8 @@ __device__ __noinline__ void cols_tma_column(const CUtensorMap *map, float2 *bf,
     if (t == 0) {
         for (int q = 0; q < nchunk; ++q)
             for (int r = 0; r < crows; r += boxr)
-                tma_store_2d(map, 0, (int)(q * cstride + c * crows + r), bf + (q * crows + r) * 16);
+                if (chk(q * cstride + c * crows + r + boxr <= nrows, CK_COL_BOX))
+                    tma_store_2d(map, 0, (int)(q * cstride + c * crows + r), bf + (q * crows + r) * 16);
         bulk_commit();
     }
 }
@@ -235,7 +237,8 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, BL)
         float2 *b0 = reinterpret_cast<float2 *>(base);
         for (int q = 0; q < nchunk; ++q)
             for (int r = 0; r < crows; r += boxr)
-                tma_load_2d(b0 + (q * crows + r) * 16, &map, 0, (int)(q * cstride + c * crows + r), &bar[0]);
+                if (chk(q * cstride + c * crows + r + boxr <= ncols * ColTmaCfg<N, GF, BL>::ROWS, CK_COL_BOX))
+                    tma_load_2d(b0 + (q * crows + r) * 16, &map, 0, (int)(q * cstride + c * crows + r), &bar[0]);
         if constexpr (!GF)
             bulk_load(base + 2 * K::BUF, hs + (c >> log2half) * hs_img + (c & hmask) * N, N * sizeof(float),
                       &bar[0]);
@@ -255,7 +258,7 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, BL)
         cols_tma_column<N, GF, BL>(&map, reinterpret_cast<float2 *>(base + b * K::BUF), h,
                            beta + (c >> log2half) * beta_img, c, kbase == 0 && (c & hmask) == 0,
                            c + gridDim.x < ncols, b, tw, log2g, base, hs, hs_img, log2half, crows, boxr, cstride,
-                           nchunk);
+                           nchunk, ncols * K::ROWS);
     }
     if (t == 0) bulk_wait_read();  // every store has read its buffer before the block's memory goes
 }
@@ -383,6 +386,8 @@ cudaError_t launch_cols_analytic(void *spec, int kind, double p0, double p1, int
         default: return cudaErrorInvalidValue;
     }
 }
+
+cudaError_t check_take_cols(unsigned out[2]) { return check_word_take(out); }
 
 cudaError_t launch_cols_filter(void *spec, const float *hs, const float *beta, long long hs_img, long long beta_img,
                                int rows, int cols, int nimg, const void *tw_rows, int *status, cudaStream_t s,

@@ -25,6 +25,7 @@
 // 0 and beta in a separate vector.
 #pragma once
 
+#include "check.cuh"
 #include "fft_core.cuh"
 #include "fft_tc.cuh"
 #include "layout.cuh"
@@ -127,10 +128,16 @@ __device__ __forceinline__ void cols_body(float2 *spec, FILT filt, int M, int lo
         const int msk = (1 << cs.ls) - 1;
         return spec + ((size_t)((s >> cs.ls) * cs.mloc + k) << cs.ls) + (s & msk);
     };
+    // checked build: every slot below N, the local column inside the block
+    // of a decomposed image (the access is skipped where a check fails)
+    auto ok = [&](int s) { return chk(s >= 0 && s < N, CK_COL_SLOT) && chk(cs.ls == 0 || k < cs.mloc, CK_COL_CHUNK); };
 
     float2 v[E];
 #pragma unroll
-    for (int e = 0; e < E; ++e) v[e] = active ? *at(slot_e<N, E, T>(t, e, log2g)) : make_float2(0.f, 0.f);
+    for (int e = 0; e < E; ++e) {
+        const int s = slot_e<N, E, T>(t, e, log2g);
+        v[e] = active && ok(s) ? *at(s) : make_float2(0.f, 0.f);
+    }
 
     float h[E];
     if constexpr (FILT::EARLY) {
@@ -168,7 +175,10 @@ __device__ __forceinline__ void cols_body(float2 *spec, FILT filt, int M, int lo
 
     if (active) {
 #pragma unroll
-        for (int e = 0; e < E; ++e) *at(slot_e<N, E, T>(t, e, log2g)) = v[e];
+        for (int e = 0; e < E; ++e) {
+            const int s = slot_e<N, E, T>(t, e, log2g);
+            if (ok(s)) *at(s) = v[e];
+        }
     }
 }
 

@@ -34,6 +34,7 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include "check.cuh"
 #include "fft_core.cuh"
 #include "tma.cuh"
 
@@ -335,7 +336,7 @@ __device__ __forceinline__ void tc5_pass16(float2 (&v)[16], float2 *sm, const fl
     asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
     if (!ok) {
         if (threadIdx.x == 0 && st.status) atomicExch(st.status, 1);
-    } else {
+    } else if (chk(32 * g + 32 <= tc5_cols(st.ngroups), CK_TC5_TMEM)) {
         uint32_t r[32];
         const uint32_t ta = st.tmem + ((uint32_t)(32 * ((threadIdx.x >> 5) & 3)) << 16) + 32u * g;
         asm volatile(

@@ -20,6 +20,7 @@
 #include <cuda.h>
 
 #include "fft_core.cuh"
+#include "check.cuh"
 #include "internal.h"
 #include "tma.cuh"
 
@@ -126,6 +127,8 @@ __global__ void __launch_bounds__(FsCfg<N, float>::MAXT, FsCfg<N, float>::MINB)
     const int w = threadIdx.x % W;
     const int t = threadIdx.x / W;
     const int j2 = blockIdx.x * W + w;
+    // checked build: the block's W columns inside n2 (uniform per block)
+    if (!chk((blockIdx.x + 1) * W <= (1 << log2n2), CK_FS_A_TILE)) return;
     if (threadIdx.x == 0) mbar_init(bar, 1);
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -218,6 +221,8 @@ __global__ void __launch_bounds__(FsCfg<N, float>::MAXT, FsCfg<N, float>::MINB)
     const int w = threadIdx.x % W;
     const int t = threadIdx.x / W;
     const int k10 = blockIdx.x * W;
+    // checked build: the block's W rows inside n1 (uniform per block)
+    if (!chk(k10 + W <= (1 << log2n1), CK_FS_B_ROWS)) return;
     if (threadIdx.x == 0) mbar_init(bar, 1);
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -249,6 +254,8 @@ __global__ void __launch_bounds__(FsCfg<N, float>::MAXT, FsCfg<N, float>::MINB)
         bulk_wait_read();
     }
 }
+
+cudaError_t check_take_fourstep(unsigned out[2]) { return check_word_take(out); }
 
 template <int N, typename R>
 static cudaError_t run_a_tma(const void *in, void *tmp, int log2n2, long long nb, int dir, const void *tw,

@@ -40,6 +40,20 @@ cudaError_t launch_fourstep_full_twiddles(void *tw, int n, int log2n2, cudaStrea
 // One block whose bounded mbarrier wait cannot succeed: sets *status after
 // `polls` tests (selftest.cu).
 cudaError_t launch_wait_timeout(int *status, unsigned polls, cudaStream_t s);
+// Index-bound check words of the GBFFT_CHECKED build (check.cuh), one per
+// translation unit that checks: read and clear (synchronous).
+cudaError_t check_take_rows(unsigned out[2]);
+cudaError_t check_take_cols(unsigned out[2]);
+cudaError_t check_take_batched(unsigned out[2]);
+cudaError_t check_take_fourstep(unsigned out[2]);
+cudaError_t check_take_tc2d(unsigned out[2]);
+cudaError_t check_take_tc5(unsigned out[2]);
+// Guard bands of a workspace (selftest.cu): write the fixed word into the n
+// guards whose byte offsets are in the device table offs; count the 4-byte
+// words that differ (or whose offset is invalid) into *bad.
+cudaError_t launch_guard_fill(char *ws, const long long *offs, int n, long long ws_bytes, cudaStream_t s);
+cudaError_t launch_guard_check(const char *ws, const long long *offs, int n, long long ws_bytes, unsigned *bad,
+                               cudaStream_t s);
 // Coarse inter-pass table of the split n = n1 n2 (n1 >= 16): entry e * n2 + j2
 // holds W_(16 n2)^(e j2) = W_n^((n1/16) e j2), e < 16, j2 < n2.
 cudaError_t launch_fourstep_coarse_twiddles(void *tw, int n2, bool dbl, cudaStream_t s);

@@ -6,6 +6,8 @@
 
 namespace gbfft {
 
+cudaError_t check_take_rows(unsigned out[2]) { return check_word_take(out); }
+
 int rows_pairs_per_block(int cols) {
     switch (ilog2(cols)) {
 #define GBFFT_CASE(L) \

@@ -15,6 +15,7 @@
 // writes Re z to row a and Im z to row b.
 #pragma once
 
+#include "check.cuh"
 #include "fft_core.cuh"
 #include "fft_tc.cuh"
 #include "layout.cuh"
@@ -96,7 +97,11 @@ __device__ __forceinline__ void rows_fwd_body(const float *__restrict__ img, flo
     const int t = threadIdx.x - g * T;
     const int p = slab.p0 + bx * G + g;
     const size_t ld = slab.ld ? (size_t)slab.ld : (size_t)N;  // column stride of the half spectra
-    const bool active = g < G;  // the grid covers exactly N/2 pairs in groups of G
+    // the grid covers exactly N/2 pairs in groups of G; a checked build also
+    // verifies the pair and the block's run of 2G slots per column (uniform
+    // per block: a block whose run fails stores nothing)
+    const bool run_ok = chk((size_t)(bx + 1) * 2 * G <= ld, CK_ROW_RUN);
+    const bool active = g < G && run_ok && chk(p < (N >> 1), CK_ROW_PAIR);
     int a, b;
     rows_of_pair(active ? p : 0, N, a, b);
 
@@ -129,6 +134,7 @@ __device__ __forceinline__ void rows_fwd_body(const float *__restrict__ img, flo
     // consecutive slots s, s + 1 of the block's run of 2G (s < G: A of pairs
     // s, s + 1; s >= G: B of pairs s - G, s - G + 1), 16 bytes per store
     float2 *sb = spec + (size_t)bx * 2 * G;
+    if (!run_ok) return;  // uniform per block
     if constexpr (TSTORE && K::PPC == 2) {
         // two pairs: each thread takes whole columns k (4 of them), reads
         // Z0[k], Z0[M-k], Z1[k], Z1[M-k] once for the four outputs A0 A1 B0 B1,
@@ -243,7 +249,8 @@ __device__ __forceinline__ void rows_inv_body(const float2 *__restrict__ spec, f
     const int t = threadIdx.x - g * T;
     const int p = slab.p0 + bx * G + g;
     const size_t ld = slab.ld ? (size_t)slab.ld : (size_t)N;  // column stride of the half spectra
-    const bool active = g < G;
+    const bool run_ok = chk((size_t)(bx + 1) * 2 * G <= ld, CK_ROW_RUN);  // uniform per block
+    const bool active = g < G && run_ok && chk(p < (N >> 1), CK_ROW_PAIR);
     int a, b;
     rows_of_pair(active ? p : 0, N, a, b);
 
@@ -258,13 +265,13 @@ __device__ __forceinline__ void rows_inv_body(const float2 *__restrict__ spec, f
     };
     if constexpr (TLOAD) {
         static_assert(K::PPC == 2, "two pairs per block");
-        if (threadIdx.x == 0) {
+        if (threadIdx.x == 0 && run_ok) {
             mbar_init(bar, 1);
             mbar_expect_tx(bar, (uint32_t)(H2 * 4 * sizeof(float2)));
             for (int k0 = 0; k0 < H2; k0 += 256) tma_load_3d(sm + (size_t)k0 * 4, imap, bx * 8, k0, z, bar);
         }
         __syncthreads();  // the barrier is initialised before anyone tests it
-        const bool ok = mbar_wait_bounded(bar, 0, kTmaPolls);
+        const bool ok = !run_ok || mbar_wait_bounded(bar, 0, kTmaPolls);
         if (__syncthreads_or(!ok)) {
             if (threadIdx.x == 0) {
                 atomicExch(status, 1);
@@ -274,7 +281,7 @@ __device__ __forceinline__ void rows_inv_body(const float2 *__restrict__ spec, f
         }
     } else {
         const float2 *sb = spec + (size_t)bx * 2 * G;
-        const int n = H2 << log2g;
+        const int n = run_ok ? H2 << log2g : 0;
         for (int idx = threadIdx.x; idx < n; idx += K::THREADS) {
             const int k = idx >> log2g, s = (idx & (G - 1)) * 2;
             const float4 x = *reinterpret_cast<const float4 *>(sb + k * ld + s);
@@ -357,6 +364,7 @@ __device__ __forceinline__ void filter_prep_tile(const float *__restrict__ hb, f
     constexpr int SR = R + 1;  // tile row stride (odd: conflict-free column writes)
     const int K = 1 << log2k, H2 = M >> 1;
     const float hsc = 0.5f * scale;
+    if (!chk(u0 + R <= N && k0 >= kbeg && k0 + K <= H2, CK_PREP_TILE)) return;  // uniform per block
 
     if (QUADS) {
         // unit = (row r, four consecutive columns); the mirror run [M-k-3, M-k]

@@ -25,6 +25,45 @@ cudaError_t launch_wait_timeout(int *status, unsigned polls, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// Guard bands of a plan's workspace (api.cu): kAlign = 256 bytes after every
+// region, filled with a fixed word at bind and checked on request.  The
+// offsets come from a table in the workspace; an offset outside the
+// workspace or misaligned (the table itself overwritten) counts as a
+// violation instead of being used.
+constexpr uint32_t kGuardWord = 0x5AA5C33Cu;
+constexpr int kGuardWords = 64;  // 256 bytes
+
+__global__ void k_guard_fill(char *ws, const long long *offs, int n, long long ws_bytes) {
+    for (int g = blockIdx.x; g < n; g += gridDim.x) {
+        const long long o = offs[g];
+        if (o < 0 || o + kGuardWords * 4 > ws_bytes || (o & 3)) continue;
+        reinterpret_cast<uint32_t *>(ws + o)[threadIdx.x] = kGuardWord;
+    }
+}
+
+__global__ void k_guard_check(const char *ws, const long long *offs, int n, long long ws_bytes, unsigned *bad) {
+    for (int g = blockIdx.x; g < n; g += gridDim.x) {
+        const long long o = offs[g];
+        const bool valid = o >= 0 && o + kGuardWords * 4 <= ws_bytes && (o & 3) == 0;
+        const bool ok = valid && reinterpret_cast<const uint32_t *>(ws + o)[threadIdx.x] == kGuardWord;
+        const unsigned nbad = __syncthreads_count(!ok);
+        if (threadIdx.x == 0 && nbad) atomicAdd(bad, nbad);
+    }
+}
+
+cudaError_t launch_guard_fill(char *ws, const long long *offs, int n, long long ws_bytes, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_guard_fill<<<n < 1024 ? n : 1024, kGuardWords, 0, s>>>(ws, offs, n, ws_bytes);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_guard_check(const char *ws, const long long *offs, int n, long long ws_bytes, unsigned *bad,
+                               cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    k_guard_check<<<n < 1024 ? n : 1024, kGuardWords, 0, s>>>(ws, offs, n, ws_bytes, bad);
+    return cudaGetLastError();
+}
+
 // Eight independent FMA chains per thread, `iters` steps each; the chains
 // stay bounded (|m| < 1) and their sum is stored only in a case that does not
 // happen, which keeps them live.

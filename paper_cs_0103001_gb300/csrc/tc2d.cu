@@ -13,6 +13,8 @@
 
 namespace gbfft {
 
+cudaError_t check_take_tc2d(unsigned out[2]) { return check_word_take(out); }
+
 template <int THREADS, int TERMS>
 __device__ __forceinline__ TcFft<TERMS> make_tc(unsigned char *smraw, size_t body_smem) {
     TcFft<TERMS> f;

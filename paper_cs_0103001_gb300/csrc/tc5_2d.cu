@@ -14,6 +14,8 @@
 
 namespace gbfft {
 
+cudaError_t check_take_tc5(unsigned out[2]) { return check_word_take(out); }
+
 template <int THREADS, int FMT> struct Tc5Smem {
     static constexpr size_t align128(size_t x) { return (x + 127) / 128 * 128; }
     // the body's shared memory, then the policy's own
