@@ -547,12 +547,21 @@ def variant_batched(count: int = 512, steps: int = 5, autotune: bool = True):
     ti = [torch.from_numpy(a).cuda() for a, _, _ in batch]
     th = [torch.from_numpy(h).cuda() for _, h, _ in batch]
     to = [torch.empty_like(a) for a in ti]
+    from paper_cs_0103001_gb300 import _native as nat
+
     plan = gb.Plan2DBatched([tuple(a.shape) for a in ti], "cuda")
     if autotune:
         plan.autotune(ti, th, to)
     ms = _timed(lambda: plan.filter(ti, th, to), steps, 2)
+    forms = {}
+    for name, form in (("per_shape_class", 0), ("persistent", 1)):
+        pf = gb.Plan2DBatched([tuple(a.shape) for a in ti], "cuda", {nat.OPT_BATCH_FORM: form})
+        forms[name] = round(_timed(lambda: pf.filter(ti, th, to), steps, 2), 3)
+        del pf
+        torch.cuda.empty_cache()
     px = sum(a.numel() for a in ti)
-    return {"images": count, "pixels": px, "ms": round(ms, 3), "images_per_s": round(count / (ms * 1e-3), 1),
+    return {"images": count, "pixels": px, "ms": round(ms, 3), "form": plan.get_option(nat.OPT_BATCH_FORM),
+            "ms_by_form": forms, "images_per_s": round(count / (ms * 1e-3), 1),
             "gbs_compulsory_12Bpx": round(12 * px / (ms * 1e-3) / 1e9, 1)}
 
 

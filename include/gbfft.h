@@ -129,7 +129,13 @@ typedef enum {
      * TMA-fed, the filter column bulk-copied beside its column; 2 = the same
      * with the filter read from global memory; 3 = one column per block.
      * Same results; other heights have one form. */
-    GBFFT_OPT_COLUMN_FORM = 10
+    GBFFT_OPT_COLUMN_FORM = 10,
+    /* Batched plans: 0 (default) = the one-shape kernels once per shape class
+     * over that class's images (reached through the image-pointer array),
+     * the filter preparations and the small classes' on-chip pipelines on a
+     * side stream; 1 = four persistent launches over largest-first work
+     * lists of every image (GBFFT_OPT_BLOCKS_PER_SM applies).  Same results. */
+    GBFFT_OPT_BATCH_FORM = 11
 } gbfft_option;
 
 /* Stages reported by gbfft_plan_profile_read. */
@@ -346,7 +352,8 @@ typedef struct {
  *     args = a gbfft_tune_args.
  *   1D plans: the one-cluster path against the four-step passes for complex64
  *     lengths 2^15..2^17 (GBFFT_OPT_ONCHIP); args = a gbfft_tune_args.
- *   Batched plans: blocks per SM of each stage (GBFFT_OPT_BLOCKS_PER_SM);
+ *   Batched plans: blocks per SM of each persistent stage
+ *     (GBFFT_OPT_BLOCKS_PER_SM), then the form (GBFFT_OPT_BATCH_FORM);
  *     args = the device image array of fft2_filter_ifft2_batched.
  *   Slab plans: nothing to tune (GBFFT_OK).
  * Results are cached in a JSON file keyed by the GPU's name and SM count and

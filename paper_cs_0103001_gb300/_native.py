@@ -42,6 +42,7 @@ OPT_BLOCKS_PER_SM = 7
 OPT_USE_GRAPH = 8
 OPT_ONCHIP = 9
 OPT_COLUMN_FORM = 10
+OPT_BATCH_FORM = 11
 
 # gbfft_filter_kind
 FILTER_GAUSSIAN = 1

@@ -223,6 +223,7 @@ class Plan2DBatched(_PlanBase):
         # device array of gbfft_image_ptrs {img, H, out}; its address stays fixed
         # so a captured graph keeps reading the current pointers
         self.ptrs = torch.zeros(n, 3, dtype=torch.int64, device=self.device)
+        self._last_table = None  # the pointers the device array holds
 
     def _set_pointers(self, imgs, Hs, outs):
         if not (len(imgs) == len(Hs) == len(outs) == len(self.shapes)):
@@ -232,8 +233,10 @@ class Plan2DBatched(_PlanBase):
             for t in (a, h, o):
                 if t.dtype != torch.float32 or tuple(t.shape[-2:]) != (r, c) or not t.is_contiguous() or not t.is_cuda:
                     raise ValueError(f"expected contiguous float32 CUDA tensors of shape ({r}, {c})")
-            table.append([a.data_ptr(), h.data_ptr(), o.data_ptr()])
-        self.ptrs.copy_(torch.tensor(table, dtype=torch.int64), non_blocking=False)
+            table.append((a.data_ptr(), h.data_ptr(), o.data_ptr()))
+        if table != self._last_table:  # the same buffers as last call: the array already holds them
+            self.ptrs.copy_(torch.tensor(table, dtype=torch.int64), non_blocking=False)
+            self._last_table = table
 
     def filter(self, imgs, Hs, outs=None):
         if outs is None:

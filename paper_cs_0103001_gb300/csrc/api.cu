@@ -86,7 +86,16 @@ struct gbfft_plan {
     // 2D: side stream for the filter preparation, forked from / joined to the
     // caller's stream with events
     cudaStream_t aux = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_join2 = nullptr;
+    // batched plans: the images grouped by shape (each class's spectra,
+    // prepared filters and betas contiguous), and the form of the launches
+    struct BatchClass {
+        int rows, cols;
+        std::vector<int> imgs;  // image indices, in input order
+        size_t off_spec, off_hs, off_beta, off_idx;
+    };
+    std::vector<BatchClass> bclasses;
+    int64_t opt_batch_form = 0;
 };
 
 namespace {
@@ -133,16 +142,26 @@ void layout_batched(gbfft_plan *p) {
             off = region_end(p, off + (size_t)len * 8);
         }
     }
-    for (BatchImage &im : p->bimgs) {
-        const size_t half_px = (size_t)im.rows * (im.cols / 2);
-        im.twc_off = (long long)p->tw_off[im.cols];
-        im.twr_off = (long long)p->tw_off[im.rows];
-        im.spec_off = (long long)off;
-        off = region_end(p, off + half_px * 8);
-        im.hs_off = (long long)off;
-        off = region_end(p, off + half_px * 4);
-        im.beta_off = (long long)off;
-        off = region_end(p, off + (size_t)im.rows * 4);
+    // per shape class: spectra [n][M/2][N], prepared filters [n][M/2][N],
+    // betas [n][N], image indices [n]; an image's regions are its slice
+    for (auto &c : p->bclasses) {
+        const size_t n = c.imgs.size(), half_px = (size_t)c.rows * (c.cols / 2);
+        c.off_spec = off;
+        off = region_end(p, off + n * half_px * 8);
+        c.off_hs = off;
+        off = region_end(p, off + n * half_px * 4);
+        c.off_beta = off;
+        off = region_end(p, off + n * (size_t)c.rows * 4);
+        c.off_idx = off;
+        off = region_end(p, off + n * sizeof(int));
+        for (size_t j = 0; j < n; ++j) {
+            BatchImage &im = p->bimgs[c.imgs[j]];
+            im.twc_off = (long long)p->tw_off[im.cols];
+            im.twr_off = (long long)p->tw_off[im.rows];
+            im.spec_off = (long long)(c.off_spec + j * half_px * 8);
+            im.hs_off = (long long)(c.off_hs + j * half_px * 4);
+            im.beta_off = (long long)(c.off_beta + j * (size_t)c.rows * 4);
+        }
     }
     layout_close(p, off);
 }
@@ -336,13 +355,64 @@ cudaError_t ensure_aux(gbfft_plan *p) {
     if (!p->aux) e = cudaStreamCreateWithFlags(&p->aux, cudaStreamNonBlocking);
     if (e == cudaSuccess && !p->ev_fork) e = cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming);
     if (e == cudaSuccess && !p->ev_join) e = cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming);
+    if (e == cudaSuccess && !p->ev_join2) e = cudaEventCreateWithFlags(&p->ev_join2, cudaEventDisableTiming);
+    return e;
+}
+
+// Batched plan, class form: the one-shape kernels once per shape class over
+// that class's images, the images reached through the caller's pointer table
+// (ImgIndirect).  Side stream: the classes' filter preparations, then the
+// small classes' one-launch on-chip pipelines; caller's stream: forward rows,
+// (join the preparations) columns and inverse rows of the other classes.
+cudaError_t batched_launch_classes(gbfft_plan *p, const gbfft_image_ptrs *ptrs, cudaStream_t s) {
+    int *status = reinterpret_cast<int *>(p->ws + p->off_status);
+    cudaError_t e = ensure_aux(p);
+    if (e == cudaSuccess) e = cudaEventRecord(p->ev_fork, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(p->aux, p->ev_fork, 0);
+    auto ind = [&](const gbfft_plan::BatchClass &c) {
+        return ImgIndirect{ptrs, reinterpret_cast<const int *>(p->ws + c.off_idx)};
+    };
+    auto onchip = [&](const gbfft_plan::BatchClass &c) { return onchip_supported(c.rows, c.cols); };
+    for (const auto &c : p->bclasses) {
+        if (e != cudaSuccess || onchip(c)) continue;
+        const long long half_px = (long long)c.rows * (c.cols / 2);
+        e = launch_filter_prep(nullptr, reinterpret_cast<float *>(p->ws + c.off_hs),
+                               reinterpret_cast<float *>(p->ws + c.off_beta), c.rows, c.cols, (int)c.imgs.size(),
+                               (float)(1.0 / ((double)c.rows * c.cols)), 0, half_px, c.rows, p->aux, 0, 0, ind(c));
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(p->ev_join, p->aux);
+    for (const auto &c : p->bclasses) {
+        if (e != cudaSuccess || !onchip(c)) continue;
+        e = launch_onchip(nullptr, nullptr, nullptr, 0, c.rows, c.cols, (int)c.imgs.size(), p->ws + p->tw_off[c.cols],
+                          p->ws + p->tw_off[c.rows], p->aux, ind(c));
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(p->ev_join2, p->aux);
+    for (const auto &c : p->bclasses) {
+        if (e != cudaSuccess || onchip(c)) continue;
+        e = launch_rows_fwd(nullptr, p->ws + c.off_spec, c.rows, c.cols, (int)c.imgs.size(), p->ws + p->tw_off[c.cols],
+                            s, Slab{0, 0}, ind(c));
+    }
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->ev_join, 0);
+    for (const auto &c : p->bclasses) {
+        if (e != cudaSuccess || onchip(c)) continue;
+        const long long half_px = (long long)c.rows * (c.cols / 2);
+        e = launch_cols_filter(p->ws + c.off_spec, reinterpret_cast<const float *>(p->ws + c.off_hs),
+                               reinterpret_cast<const float *>(p->ws + c.off_beta), half_px, c.rows, c.rows, c.cols,
+                               (int)c.imgs.size(), p->ws + p->tw_off[c.rows], status, s);
+    }
+    for (const auto &c : p->bclasses) {
+        if (e != cudaSuccess || onchip(c)) continue;
+        e = launch_rows_inv(p->ws + c.off_spec, nullptr, c.rows, c.cols, (int)c.imgs.size(), p->ws + p->tw_off[c.cols],
+                            status, s, Slab{0, 0}, ind(c));
+    }
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->ev_join2, 0);
     return e;
 }
 
 // The four stages of a batched plan: the filter preparation on the plan's side
 // stream beside the forward row pass (it touches no spectrum), joined before
 // the column pass; under stream capture the side stream joins the capture.
-cudaError_t batched_launch_all(gbfft_plan *p, const gbfft_image_ptrs *ptrs, cudaStream_t s, const int *grid) {
+cudaError_t batched_launch_persistent(gbfft_plan *p, const gbfft_image_ptrs *ptrs, cudaStream_t s, const int *grid) {
     const BatchImage *imgs = reinterpret_cast<const BatchImage *>(p->ws + p->off_bimgs);
     auto stage = [&](int st, cudaStream_t on) {
         const BatchItem *items = reinterpret_cast<const BatchItem *>(p->ws + p->off_bitems[st]);
@@ -359,6 +429,10 @@ cudaError_t batched_launch_all(gbfft_plan *p, const gbfft_image_ptrs *ptrs, cuda
     if (e == cudaSuccess) e = stage(1, s);  // columns
     if (e == cudaSuccess) e = stage(2, s);  // inverse rows
     return e;
+}
+
+cudaError_t batched_launch_all(gbfft_plan *p, const gbfft_image_ptrs *ptrs, cudaStream_t s, const int *grid) {
+    return p->opt_batch_form == 1 ? batched_launch_persistent(p, ptrs, s, grid) : batched_launch_classes(p, ptrs, s);
 }
 
 void drop_graph(gbfft_plan *p) {
@@ -475,6 +549,11 @@ int fft_plan_set_option(gbfft_plan_t p, int key, int64_t value) {
             p->opt_backward = value;
             layout(p);
             return GBFFT_OK;
+        case GBFFT_OPT_BATCH_FORM:
+            if (p->kind != KIND_BATCH || (value != 0 && value != 1)) return GBFFT_ERR_INVALID_VALUE;
+            p->opt_batch_form = value;
+            drop_graph(p);
+            return GBFFT_OK;
         case GBFFT_OPT_COLUMN_FORM:
             if ((p->kind != KIND_2D && p->kind != KIND_SLAB) || value < 0 || value > 3) return GBFFT_ERR_INVALID_VALUE;
             p->opt_colform = value;
@@ -542,6 +621,10 @@ int fft_plan_bind_workspace(gbfft_plan_t p, void *workspace, size_t bytes, gbfft
                                     p->bitems[st].size() * sizeof(BatchItem), cudaMemcpyHostToDevice, s);
             for (const auto &kv : p->tw_off)
                 if (e == cudaSuccess) e = launch_twiddles(p->ws + kv.second, kv.first, false, s);
+            for (const auto &c : p->bclasses)
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(p->ws + c.off_idx, c.imgs.data(), c.imgs.size() * sizeof(int),
+                                        cudaMemcpyHostToDevice, s);
             return e;
         });
     }
@@ -954,6 +1037,21 @@ int fft2_batched_plan_create(int count, const int64_t *rows, const int64_t *cols
                          [](const Costed &a, const Costed &b) { return a.cost > b.cost; });
         for (const Costed &c : work[st]) p->bitems[st].push_back(c.it);
     }
+    // shape classes, the largest images first (their launches fill the GPU
+    // while the small classes run beside them)
+    std::map<std::pair<int, int>, int> cls;
+    for (int i = 0; i < count; ++i) {
+        const auto key = std::make_pair((int)rows[i], (int)cols[i]);
+        auto it = cls.find(key);
+        if (it == cls.end()) {
+            it = cls.emplace(key, (int)p->bclasses.size()).first;
+            p->bclasses.push_back(gbfft_plan::BatchClass{(int)rows[i], (int)cols[i], {}, 0, 0, 0, 0});
+        }
+        p->bclasses[it->second].imgs.push_back(i);
+    }
+    std::stable_sort(p->bclasses.begin(), p->bclasses.end(), [](const auto &a, const auto &b) {
+        return (long long)a.rows * a.cols > (long long)b.rows * b.cols;
+    });
     layout(p);
     *out = p;
     return GBFFT_OK;
@@ -975,6 +1073,9 @@ int fft2_filter_ifft2_batched(gbfft_plan_t p, const gbfft_image_ptrs *images, gb
     if (!p->opt_graph && !p->opt_profile) {
         e = batched_launch_all(p, images, s, grid);
         return e == cudaSuccess ? GBFFT_OK : cuda_fail(e);
+    }
+    if (!p->opt_graph && p->opt_batch_form != 1) {  // profiling the class form: one event pair around it
+        return launch(p, GBFFT_STAGE_GRAPH, s, [&] { return batched_launch_classes(p, images, s); });
     }
     if (!p->opt_graph) {  // profiling: every stage alone on the caller's stream
         for (int st : kBatchOrder) {
@@ -1086,7 +1187,10 @@ bool apply_tuned(gbfft_plan *p, const TuneEntry &e) {
             snprintf(k, sizeof k, "bps%d", st);
             if (!get(k, &v[st]) || v[st] < 1 || v[st] > 64) return false;
         }
+        int64_t form = 0;
+        if (!get("form", &form) || form < 0 || form > 1) return false;
         for (int st = 0; st < kBatchStages; ++st) p->opt_bps[st] = v[st];
+        p->opt_batch_form = form;
         drop_graph(p);
         return true;
     }
@@ -1219,7 +1323,29 @@ int tune_batched(gbfft_plan *p, const gbfft_image_ptrs *images, cudaStream_t s, 
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     drop_graph(p);
-    return e == cudaSuccess ? GBFFT_OK : cuda_fail(e);
+    if (e != cudaSuccess) return cuda_fail(e);
+    // then the form: per shape class (default) against the persistent launches
+    for (int q = 0; q < kBatchStages; ++q) grid[q] = (int)p->opt_bps[q] * nsm;
+    float best = 0.f, first = 0.f;
+    int best_form = 0;
+    for (int form : {0, 1}) {
+        p->opt_batch_form = form;
+        float ms = 0.f;
+        e = time_median(s, 5, [&] { return batched_launch_all(p, images, s, grid) == cudaSuccess ? GBFFT_OK : GBFFT_ERR_CUDA; },
+                        &ms);
+        if (e != cudaSuccess) return cuda_fail(e);
+        if (form == 0) first = ms;
+        if (form == 0 || ms < 0.99f * best) {
+            best = ms;
+            best_form = form;
+        }
+    }
+    p->opt_batch_form = best_form;
+    drop_graph(p);
+    out["form"] = best_form;
+    out["us"] = 1e3 * best;
+    out["us_first_candidate"] = 1e3 * first;
+    return GBFFT_OK;
 }
 
 }  // namespace
@@ -1277,6 +1403,7 @@ int fft_plan_get_option(gbfft_plan_t p, int key, int64_t *value) {
         case GBFFT_OPT_USE_GRAPH: *value = p->opt_graph; return GBFFT_OK;
         case GBFFT_OPT_ONCHIP: *value = p->opt_onchip; return GBFFT_OK;
         case GBFFT_OPT_COLUMN_FORM: *value = p->opt_colform; return GBFFT_OK;
+        case GBFFT_OPT_BATCH_FORM: *value = p->opt_batch_form; return GBFFT_OK;
         default: return GBFFT_ERR_INVALID_VALUE;
     }
 }
@@ -1342,6 +1469,7 @@ int fft_plan_destroy(gbfft_plan_t p) {
     if (p->aux) cudaStreamDestroy(p->aux);
     if (p->ev_fork) cudaEventDestroy(p->ev_fork);
     if (p->ev_join) cudaEventDestroy(p->ev_join);
+    if (p->ev_join2) cudaEventDestroy(p->ev_join2);
     for (auto &r : p->prof) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);

@@ -91,15 +91,16 @@ cudaError_t launch_cols_spectrum(const void *spec, float *mag_T, float *nyq, flo
 // Forward row pass: nimg real images [rows][cols] -> half spectra
 // [nimg][cols/2][rows] complex64, slot order (layout.cuh).
 // With a slab (one image): only pairs slab.p0 .., into [cols/2][slab.ld].
+// ind.ptrs != nullptr: image z of the launch at ind.ptrs[ind.idx[z]].img (img unused).
 cudaError_t launch_rows_fwd(const float *img, void *spec, int rows, int cols, int nimg, const void *tw_cols,
-                            cudaStream_t s, Slab slab = Slab{0, 0});
+                            cudaStream_t s, Slab slab = Slab{0, 0}, ImgIndirect ind = ImgIndirect{nullptr, nullptr});
 // Prepared filter (rows_impl.cuh) for nimg filters H + i * h_stride into
 // hs + i * hs_img, beta + i * beta_img.  kcnt > 0: only the half-spectrum
 // columns kbeg .. kbeg + kcnt - 1, written as hs columns 0 .. kcnt - 1 (beta
 // only when the range holds column 0).
 cudaError_t launch_filter_prep(const float *H, float *hs, float *beta, int rows, int cols, int nimg, float scale,
                                long long h_stride, long long hs_img, long long beta_img, cudaStream_t s,
-                               int kbeg = 0, int kcnt = 0);
+                               int kbeg = 0, int kcnt = 0, ImgIndirect ind = ImgIndirect{nullptr, nullptr});
 // Column pass with an analytic filter computed in the kernel (no filter
 // array): kind 1 Gaussian (p0 = sigma in bins), 2 Butterworth (p0 = order,
 // p1 = cutoff D0 in bins), 3 disc of Eq. filtro (p0 = radius b); cols_impl.cuh.
@@ -115,13 +116,15 @@ cudaError_t launch_cols_filter(void *spec, const float *hs, const float *beta, l
                                int rows, int cols, int nimg, const void *tw_rows, int *status, cudaStream_t s,
                                ColSlab cs = ColSlab{0, 0, 0}, int form = 0);
 cudaError_t launch_rows_inv(const void *spec, float *out, int rows, int cols, int nimg, const void *tw_cols,
-                            int *status, cudaStream_t s, Slab slab = Slab{0, 0});
+                            int *status, cudaStream_t s, Slab slab = Slab{0, 0},
+                            ImgIndirect ind = ImgIndirect{nullptr, nullptr});
 // Tensor-core variants (tc2d.cu): radix-16 passes as split-BF16 DFT-matrix
 // products with `terms` = 2 or 3 BF16 parts per operand; sides 512..4096.
 bool tc_supported(int rows, int cols);
 bool onchip_supported(int rows, int cols);
 cudaError_t launch_onchip(const float *img, const float *H, float *out, long long h_stride, int rows, int cols,
-                          int nimg, const void *tw_cols, const void *tw_rows, cudaStream_t s);
+                          int nimg, const void *tw_cols, const void *tw_rows, cudaStream_t s,
+                          ImgIndirect ind = ImgIndirect{nullptr, nullptr});
 cudaError_t launch_rows_tc(bool fwd, const void *src, void *dst, int rows, int cols, int nimg, const void *tw,
                            int terms, cudaStream_t s);
 cudaError_t launch_cols_tc(void *spec, const float *hs, const float *beta, long long hs_img, long long beta_img,

@@ -18,7 +18,18 @@
 // G = 4) and the inverse row pass reads them back the same way.
 #pragma once
 
+#include "gbfft.h"
+
 namespace gbfft {
+
+// Images of a launch given by the caller's device table of per-image
+// pointers (a batched call): image z of the launch is ptrs[idx[z]], idx being
+// the plan's list of the images of one shape.  ptrs == nullptr: the images
+// are contiguous (base + z x image size), as in a one-shape plan.
+struct ImgIndirect {
+    const gbfft_image_ptrs *ptrs;
+    const int *idx;
+};
 
 // Row-slab share of an image decomposed over ranks (Sec. 2's division of the
 // work among processes, here by rows): a rank owns the pairs p0 .. p0 + P - 1

@@ -60,7 +60,7 @@ template <int R, int PP> __device__ __forceinline__ void owner_of(int u, int &ct
 template <int R, int M>
 __global__ void __launch_bounds__(OnChipCfg<R, M>::THREADS)
     k_onchip(const float *__restrict__ img, const float *__restrict__ H, float *__restrict__ out, long long h_stride,
-             float scale, const float2 *__restrict__ twm, const float2 *__restrict__ twr) {
+             float scale, const float2 *__restrict__ twm, const float2 *__restrict__ twr, ImgIndirect ind) {
     typedef OnChipCfg<R, M> K;
     constexpr int E = K::E, PP = K::PP, SRS = K::SRS, H2 = M / 2;
     extern __shared__ __align__(16) unsigned char smraw[];
@@ -72,9 +72,16 @@ __global__ void __launch_bounds__(OnChipCfg<R, M>::THREADS)
     cg::cluster_group cl = cg::this_cluster();
     const int c = (int)cl.block_rank();
     const size_t z = blockIdx.y;
-    img += z * R * M;
-    out += z * R * M;
-    H += z * h_stride;
+    if (ind.ptrs) {
+        const gbfft_image_ptrs pp = ind.ptrs[ind.idx[z]];
+        img = pp.img;
+        H = pp.H;
+        out = pp.out;
+    } else {
+        img += z * R * M;
+        out += z * R * M;
+        H += z * h_stride;
+    }
 
     // ---- 1. forward rows and the filter of their frequency rows
     {
@@ -251,7 +258,7 @@ __global__ void __launch_bounds__(OnChipCfg<R, M>::THREADS)
 
 template <int R, int M>
 static cudaError_t onchip_launch(const float *img, const float *H, float *out, long long h_stride, int nimg,
-                                 const void *twm, const void *twr, cudaStream_t s) {
+                                 const void *twm, const void *twr, cudaStream_t s, ImgIndirect ind) {
     typedef OnChipCfg<R, M> K;
     const void *kern = (const void *)k_onchip<R, M>;
     cudaError_t e = set_smem_attrs(kern, K::SMEM);
@@ -271,9 +278,10 @@ static cudaError_t onchip_launch(const float *img, const float *H, float *out, l
         at[0].val.clusterDim.z = 1;
         cfg.attrs = at;
         cfg.numAttrs = 1;
-        e = cudaLaunchKernelEx(&cfg, k_onchip<R, M>, img + (size_t)z0 * R * M, H + (size_t)z0 * h_stride,
-                               out + (size_t)z0 * R * M, h_stride, scale, static_cast<const float2 *>(twm),
-                               static_cast<const float2 *>(twr));
+        const ImgIndirect iz{ind.ptrs, ind.ptrs ? ind.idx + z0 : nullptr};
+        e = cudaLaunchKernelEx(&cfg, k_onchip<R, M>, ind.ptrs ? img : img + (size_t)z0 * R * M,
+                               ind.ptrs ? H : H + (size_t)z0 * h_stride, ind.ptrs ? out : out + (size_t)z0 * R * M,
+                               h_stride, scale, static_cast<const float2 *>(twm), static_cast<const float2 *>(twr), iz);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
@@ -285,11 +293,12 @@ bool onchip_supported(int rows, int cols) { return rows >= 16 && rows <= 256 && 
 #define GBFFT_OC_ALL(X) GBFFT_OC_COLS(4, X) GBFFT_OC_COLS(5, X) GBFFT_OC_COLS(6, X) GBFFT_OC_COLS(7, X) GBFFT_OC_COLS(8, X)
 
 cudaError_t launch_onchip(const float *img, const float *H, float *out, long long h_stride, int rows, int cols,
-                          int nimg, const void *tw_cols, const void *tw_rows, cudaStream_t s) {
+                          int nimg, const void *tw_cols, const void *tw_rows, cudaStream_t s, ImgIndirect ind) {
     if (nimg <= 0) return cudaSuccess;
     switch (ilog2(rows) * 16 + ilog2(cols)) {
 #define GBFFT_C(LR, LC) \
-    case LR * 16 + LC: return onchip_launch<(1 << LR), (1 << LC)>(img, H, out, h_stride, nimg, tw_cols, tw_rows, s);
+    case LR * 16 + LC:                                                                                         \
+        return onchip_launch<(1 << LR), (1 << LC)>(img, H, out, h_stride, nimg, tw_cols, tw_rows, s, ind);
         GBFFT_OC_ALL(GBFFT_C)
 #undef GBFFT_C
         default: return cudaErrorInvalidValue;

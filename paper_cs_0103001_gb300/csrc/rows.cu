@@ -23,21 +23,23 @@ int rows_pairs_per_block(int cols) {
 template <int M>
 __global__ void __launch_bounds__(RowCfg<M>::THREADS, RowCfg<M>::THREADS <= 512 ? 2 : 1)
     k_rows_fwd(const float *__restrict__ img, float2 *__restrict__ spec, int N, int log2g,
-               const float2 *__restrict__ tw, Slab slab) {
+               const float2 *__restrict__ tw, Slab slab, ImgIndirect ind) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const size_t y = blockIdx.y;
-    rows_fwd_body<M>(img + y * N * M, spec + y * (M / 2) * N, N, log2g, tw, blockIdx.x, smraw, Fp32Fft(),
-                     Crop{0, 0}, nullptr, 0, slab);
+    const float *im = ind.ptrs ? ind.ptrs[ind.idx[y]].img : img + y * N * M;
+    rows_fwd_body<M>(im, spec + y * (M / 2) * N, N, log2g, tw, blockIdx.x, smraw, Fp32Fft(), Crop{0, 0}, nullptr, 0,
+                     slab);
 }
 
 template <int M>
 __global__ void __launch_bounds__(RowCfg<M>::THREADS, RowCfg<M>::THREADS <= 512 ? 2 : 1)
     k_rows_inv(const float2 *__restrict__ spec, float *__restrict__ out, int N, int log2g,
-               const float2 *__restrict__ tw, Slab slab) {
+               const float2 *__restrict__ tw, Slab slab, ImgIndirect ind) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const size_t y = blockIdx.y;
-    rows_inv_body<M>(spec + y * (M / 2) * N, out + y * N * M, N, log2g, tw, blockIdx.x, smraw, Fp32Fft(),
-                     Crop{0, 0}, nullptr, 0, nullptr, nullptr, slab);
+    float *o = ind.ptrs ? ind.ptrs[ind.idx[y]].out : out + y * N * M;
+    rows_inv_body<M>(spec + y * (M / 2) * N, o, N, log2g, tw, blockIdx.x, smraw, Fp32Fft(), Crop{0, 0}, nullptr, 0,
+                     nullptr, nullptr, slab);
 }
 
 // Row passes of a zero-padded image (Sec. 5 application path): image y of the
@@ -73,16 +75,18 @@ __global__ void __launch_bounds__(RowCfg<M>::THREADS, RowCfg<M>::THREADS <= 512 
 template <int R, bool QUADS>
 __global__ void __launch_bounds__(256)
     k_filter_prep(const float *__restrict__ H, float *__restrict__ hs, float *__restrict__ beta, int N, int M,
-                  int log2k, float scale, long long h_stride, long long hs_img, long long beta_img, int kbeg) {
+                  int log2k, float scale, long long h_stride, long long hs_img, long long beta_img, int kbeg,
+                  ImgIndirect ind) {
     extern __shared__ __align__(16) unsigned char smraw[];
     const size_t z = blockIdx.z;
-    filter_prep_tile<R, QUADS>(H + z * h_stride, hs + z * hs_img, beta + z * beta_img, N, M, log2k, scale,
+    const float *hz = ind.ptrs ? ind.ptrs[ind.idx[z]].H : H + z * h_stride;
+    filter_prep_tile<R, QUADS>(hz, hs + z * hs_img, beta + z * beta_img, N, M, log2k, scale,
                                blockIdx.x * R, kbeg + (blockIdx.y << log2k), reinterpret_cast<float *>(smraw), kbeg);
 }
 
 cudaError_t launch_filter_prep(const float *H, float *hs, float *beta, int rows, int cols, int nimg, float scale,
                                long long h_stride, long long hs_img, long long beta_img, cudaStream_t s, int kbeg,
-                               int kcnt) {
+                               int kcnt, ImgIndirect ind) {
     const int ncol = kcnt > 0 ? kcnt : cols / 2;  // half-spectrum columns to prepare
     const int kk = ncol < kPrepCols ? ncol : kPrepCols;
     const int rr = rows < kPrepRows ? rows : kPrepRows;  // rows per tile
@@ -96,7 +100,7 @@ cudaError_t launch_filter_prep(const float *H, float *hs, float *beta, int rows,
         e = set_smem_attrs((const void *)k_filter_prep<RR, Q>, smem);                                          \
         if (e != cudaSuccess) return e;                                                                        \
         k_filter_prep<RR, Q><<<grid, 256, smem, s>>>(H, hs, beta, rows, cols, ilog2(kk), scale, h_stride, hs_img, \
-                                                     beta_img, kbeg);                                          \
+                                                     beta_img, kbeg, ind);                                     \
         return cudaGetLastError();
         GBFFT_R(2, false) GBFFT_R(4, false) GBFFT_R(8, false) GBFFT_R(16, false) GBFFT_R(32, false)
         GBFFT_R(4, true) GBFFT_R(8, true) GBFFT_R(16, true) GBFFT_R(32, true)
@@ -120,12 +124,14 @@ static int log2_pairs_per_block(int rows, int cols) {
 template <int M>
 __global__ void __launch_bounds__(RowCfg<M>::THREADS, RowCfg<M>::THREADS <= 512 ? 2 : 1)
     k_rows_fwd_tma(const float *__restrict__ img, float2 *__restrict__ spec, int N, int log2g,
-                   const float2 *__restrict__ tw, const __grid_constant__ CUtensorMap omap, Slab slab) {
+                   const float2 *__restrict__ tw, const __grid_constant__ CUtensorMap omap, Slab slab,
+                   ImgIndirect ind) {
     extern __shared__ __align__(1024) unsigned char smraw[];
     unsigned char *base = smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u);  // the box's swizzle period
     const size_t y = blockIdx.y;
-    rows_fwd_body<M, Fp32Fft, false, true>(img + y * N * M, spec + y * (M / 2) * N, N, log2g, tw, blockIdx.x, base,
-                                           Fp32Fft(), Crop{0, 0}, &omap, (int)y, slab);
+    const float *im = ind.ptrs ? ind.ptrs[ind.idx[y]].img : img + y * N * M;
+    rows_fwd_body<M, Fp32Fft, false, true>(im, spec + y * (M / 2) * N, N, log2g, tw, blockIdx.x, base, Fp32Fft(),
+                                           Crop{0, 0}, &omap, (int)y, slab);
 }
 
 // Tensor map of the half spectra of nimg images ({2 rows floats, cols/2
@@ -148,7 +154,7 @@ static bool spec_map(CUtensorMap *map, void *spec, int rows, int cols, int nimg,
 // [M/2][slab.ld] (the launcher's caller checks that they fill whole blocks)
 template <int M>
 static cudaError_t run_rows_fwd(const float *img, void *spec, int rows, int nimg, const void *tw, cudaStream_t s,
-                                Slab slab) {
+                                Slab slab, ImgIndirect ind) {
     typedef RowCfg<M> K;
     const int ld = slab.ld ? slab.ld : rows;  // column stride of the half spectra written
     if constexpr (M >= 256 && 4 * K::PPC <= 256 && K::THREADS <= 512) {
@@ -160,7 +166,7 @@ static cudaError_t run_rows_fwd(const float *img, void *spec, int rows, int nimg
             if (e != cudaSuccess) return e;
             dim3 grid((ld / 2) >> lg, nimg);
             k_rows_fwd_tma<M><<<grid, K::THREADS, smem, s>>>(img, static_cast<float2 *>(spec), rows, lg,
-                                                             static_cast<const float2 *>(tw), map, slab);
+                                                             static_cast<const float2 *>(tw), map, slab, ind);
             return cudaGetLastError();
         }
     }
@@ -169,7 +175,7 @@ static cudaError_t run_rows_fwd(const float *img, void *spec, int rows, int nimg
     const int lg = log2_pairs_per_block(rows, M);
     dim3 grid((ld / 2) >> lg, nimg);
     k_rows_fwd<M><<<grid, K::THREADS, K::SMEM_FWD, s>>>(img, static_cast<float2 *>(spec), rows, lg,
-                                                    static_cast<const float2 *>(tw), slab);
+                                                    static_cast<const float2 *>(tw), slab, ind);
     return cudaGetLastError();
 }
 
@@ -178,19 +184,20 @@ static cudaError_t run_rows_fwd(const float *img, void *spec, int rows, int nimg
 template <int M>
 __global__ void __launch_bounds__(RowCfg<M>::THREADS, 2)
     k_rows_inv_tma(float *__restrict__ out, int N, int log2g, const float2 *__restrict__ tw,
-                   const __grid_constant__ CUtensorMap imap, int *status, Slab slab) {
+                   const __grid_constant__ CUtensorMap imap, int *status, Slab slab, ImgIndirect ind) {
     extern __shared__ __align__(1024) unsigned char smraw[];
     unsigned char *base = smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u);  // the box's swizzle period
     uint64_t *bar = reinterpret_cast<uint64_t *>(base + RowCfg<M>::SMEM);
     const size_t y = blockIdx.y;
-    rows_inv_body<M, Fp32Fft, false, true>(nullptr, out + y * N * M, N, log2g, tw, blockIdx.x, base, Fp32Fft(),
-                                           Crop{0, 0}, &imap, (int)y, bar, status, slab);
+    float *o = ind.ptrs ? ind.ptrs[ind.idx[y]].out : out + y * N * M;
+    rows_inv_body<M, Fp32Fft, false, true>(nullptr, o, N, log2g, tw, blockIdx.x, base, Fp32Fft(), Crop{0, 0}, &imap,
+                                           (int)y, bar, status, slab);
 }
 
 // slab.ld > 0: one image, pairs slab.p0 .. from [M/2][slab.ld]
 template <int M>
 static cudaError_t run_rows_inv(const void *spec, float *out, int rows, int nimg, const void *tw, int *status,
-                                cudaStream_t s, Slab slab) {
+                                cudaStream_t s, Slab slab, ImgIndirect ind) {
     typedef RowCfg<M> K;
     const int ld = slab.ld ? slab.ld : rows;  // column stride of the half spectra read
     if constexpr (K::PPC == 2 && K::THREADS <= 512) {
@@ -202,7 +209,7 @@ static cudaError_t run_rows_inv(const void *spec, float *out, int rows, int nimg
             if (e != cudaSuccess) return e;
             dim3 grid((ld / 2) >> lg, nimg);
             k_rows_inv_tma<M><<<grid, K::THREADS, smem, s>>>(out, rows, lg, static_cast<const float2 *>(tw), map,
-                                                             status, slab);
+                                                             status, slab, ind);
             return cudaGetLastError();
         }
     }
@@ -211,7 +218,7 @@ static cudaError_t run_rows_inv(const void *spec, float *out, int rows, int nimg
     const int lg = log2_pairs_per_block(rows, M);
     dim3 grid((ld / 2) >> lg, nimg);
     k_rows_inv<M><<<grid, K::THREADS, K::SMEM, s>>>(static_cast<const float2 *>(spec), out, rows, lg,
-                                                    static_cast<const float2 *>(tw), slab);
+                                                    static_cast<const float2 *>(tw), slab, ind);
     return cudaGetLastError();
 }
 
@@ -249,10 +256,10 @@ cudaError_t launch_rows_pad(bool fwd, const void *src, void *dst, int rows, int 
 }
 
 cudaError_t launch_rows_fwd(const float *img, void *spec, int rows, int cols, int nimg, const void *tw_cols,
-                            cudaStream_t s, Slab slab) {
+                            cudaStream_t s, Slab slab, ImgIndirect ind) {
     switch (ilog2(cols)) {
 #define GBFFT_CASE(L) \
-    case L: return run_rows_fwd<(1 << L)>(img, spec, rows, nimg, tw_cols, s, slab);
+    case L: return run_rows_fwd<(1 << L)>(img, spec, rows, nimg, tw_cols, s, slab, ind);
         GBFFT_CASE(1) GBFFT_CASE(2) GBFFT_CASE(3) GBFFT_CASE(4) GBFFT_CASE(5) GBFFT_CASE(6) GBFFT_CASE(7)
         GBFFT_CASE(8) GBFFT_CASE(9) GBFFT_CASE(10) GBFFT_CASE(11) GBFFT_CASE(12) GBFFT_CASE(13)
 #undef GBFFT_CASE
@@ -261,10 +268,10 @@ cudaError_t launch_rows_fwd(const float *img, void *spec, int rows, int cols, in
 }
 
 cudaError_t launch_rows_inv(const void *spec, float *out, int rows, int cols, int nimg, const void *tw_cols,
-                            int *status, cudaStream_t s, Slab slab) {
+                            int *status, cudaStream_t s, Slab slab, ImgIndirect ind) {
     switch (ilog2(cols)) {
 #define GBFFT_CASE(L) \
-    case L: return run_rows_inv<(1 << L)>(spec, out, rows, nimg, tw_cols, status, s, slab);
+    case L: return run_rows_inv<(1 << L)>(spec, out, rows, nimg, tw_cols, status, s, slab, ind);
         GBFFT_CASE(1) GBFFT_CASE(2) GBFFT_CASE(3) GBFFT_CASE(4) GBFFT_CASE(5) GBFFT_CASE(6) GBFFT_CASE(7)
         GBFFT_CASE(8) GBFFT_CASE(9) GBFFT_CASE(10) GBFFT_CASE(11) GBFFT_CASE(12) GBFFT_CASE(13)
 #undef GBFFT_CASE
