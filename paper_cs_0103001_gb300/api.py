@@ -209,8 +209,10 @@ class Plan2D(_PlanBase):
 
 class Plan2DBatched(_PlanBase):
     """Sec. 5 pipeline over images of uneven power-of-two sizes (16..4096 per
-    side), each with its own filter, in four persistent launches (optionally
-    replayed from a CUDA graph).  `shapes` is a list of (rows, cols)."""
+    side), each with its own filter: the one-shape kernels once per shape
+    class (default), or four persistent launches over all images
+    (GBFFT_OPT_BATCH_FORM = 1); optionally replayed from a CUDA graph.
+    `shapes` is a list of (rows, cols)."""
 
     def __init__(self, shapes, device, options=None):
         n = len(shapes)
@@ -224,6 +226,7 @@ class Plan2DBatched(_PlanBase):
         # so a captured graph keeps reading the current pointers
         self.ptrs = torch.zeros(n, 3, dtype=torch.int64, device=self.device)
         self._last_table = None  # the pointers the device array holds
+        self._bound = None  # the buffers of bind(), kept alive for run()
 
     def _set_pointers(self, imgs, Hs, outs):
         if not (len(imgs) == len(Hs) == len(outs) == len(self.shapes)):
@@ -242,15 +245,33 @@ class Plan2DBatched(_PlanBase):
         if outs is None:
             outs = [torch.empty_like(a) for a in imgs]
         with self.lock:
+            self._bound = None
             self._set_pointers(imgs, Hs, outs)
             nat.call("fft2_filter_ifft2_batched", self.handle, _ptr(self.ptrs), _stream_handle(self.device))
         return outs
+
+    def bind(self, imgs, Hs, outs):
+        """Check and record the buffers once; run() then filters them again
+        with no per-call checks (fixed input and output buffers, as in a
+        serving loop).  The buffers must stay alive while bound."""
+        with self.lock:
+            self._set_pointers(imgs, Hs, outs)
+            self._bound = (imgs, Hs, outs)
+
+    def run(self):
+        """The pipeline over the buffers of the last bind() (a filter() call
+        in between unbinds them)."""
+        if self._bound is None:
+            raise RuntimeError("run() needs buffers: call bind() first")
+        with self.lock:
+            nat.call("fft2_filter_ifft2_batched", self.handle, _ptr(self.ptrs), _stream_handle(self.device))
 
     def autotune(self, imgs, Hs, outs=None):
         """Time the launch shapes on these inputs and keep the fastest."""
         if outs is None:
             outs = [torch.empty_like(a) for a in imgs]
         with self.lock:
+            self._bound = None
             self._set_pointers(imgs, Hs, outs)
             nat.call("fft_plan_autotune", self.handle, _ptr(self.ptrs), _stream_handle(self.device))
         return self.get_option(nat.OPT_BLOCKS_PER_SM)

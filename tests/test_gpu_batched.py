@@ -92,6 +92,29 @@ def test_new_pointers_reach_the_captured_graph(gb):
             assert rel_l2(o.cpu().numpy(), oracle.pipeline(a, h)) <= tol_fp32(r * c)
 
 
+def test_bind_and_run(gb):
+    """run() over bound buffers gives filter()'s numbers; a filter() call
+    unbinds, so run() then refuses."""
+    import torch
+
+    imgs, Hs = _inputs(SHAPES, 44)
+    ti = [torch.from_numpy(a).cuda() for a in imgs]
+    th = [torch.from_numpy(h).cuda() for h in Hs]
+    plan = gb.Plan2DBatched(SHAPES, "cuda")
+    with pytest.raises(RuntimeError):
+        plan.run()
+    ref = [o.clone() for o in plan.filter(ti, th)]
+    outs = [torch.full_like(a, float("nan")) for a in ti]
+    plan.bind(ti, th, outs)
+    plan.run()
+    plan.run()
+    for a, b in zip(ref, outs):
+        assert torch.equal(a, b)
+    plan.filter(ti, th)
+    with pytest.raises(RuntimeError):
+        plan.run()
+
+
 def test_autotune_keeps_results(gb):
     import torch
 
