@@ -54,7 +54,8 @@ def test_one_pass_all_sizes(gb, log2n, batch, dbl):
 
 
 @pytest.mark.parametrize("dbl,log2n,batch", [
-    (False, 15, 3), (False, 16, 2), (False, 17, 3), (False, 18, 1), (False, 20, 2), (False, 22, 1),
+    (False, 15, 3), (False, 16, 2), (False, 17, 3), (False, 18, 1), (False, 20, 2), (False, 21, 1), (False, 22, 1),
+    (False, 23, 1), (False, 24, 1),
     (True, 14, 3), (True, 15, 2), (True, 17, 1), (True, 19, 2),
 ])
 def test_four_step(gb, dbl, log2n, batch):
