@@ -436,6 +436,7 @@ def run_gbfft(args):
             "variants": dict(run_variants(), pipeline4096_precision=_guard(lambda: variant_precision(img, H, ref, flush)),
                              pipeline4096_column_forms=_guard(lambda: variant_column_forms(img, H, flush)),
                              pipeline4096_analytic_filter=_guard(lambda: variant_analytic(img, flush)),
+                             pipeline4096_images_per_call=_guard(lambda: variant_images_per_call(img, H, flush)),
                              cufft_context=_guard(lambda: variant_cufft_context(img, H, ref, flush)))
             if args.variants else None,
             "alu_peaks_measured": _guard(lambda: {"fp64_fma_gflops": round(gb.measure_fma_peak(True) / 1e9, 1),
@@ -684,6 +685,43 @@ def variant_analytic(img, flush, steps: int = 100):
     ms = _timed(lambda: plan.filter_analytic(img, nat.FILTER_BUTTERWORTH, 4, d0, out=out), steps, 5, flush)
     return {"us": round(ms * 1e3, 2), "gbs_44Bpx": round(METRIC_BYTES_PER_PX * ROWS * COLS / (ms * 1e-3) / 1e9, 1),
             "filter": "butterworth order 4, D0 = 0.1 Nyquist, by formula"}
+
+
+def variant_images_per_call(img, H, flush, steps: int = 30):
+    """The headline image and filter, n = 1, 2, 4, 8 copies in one call
+    (a plan with batch n, shared filter): time per image and the stages'
+    times per image.  Each stage launch carries a fixed cost (the last
+    partial wave of its blocks, its ramp-up and launch latency) that n
+    images share; the per-image times at n = 8 are the kernels' streaming
+    rate.  frac_algorithmic: the schedule's bytes per image (26 B/px for the
+    three transform stages plus the shared filter's preparation, 6 B/px once
+    per call) over the time per image, against the measured HBM bandwidth."""
+    import torch
+
+    import paper_cs_0103001_gb300 as gb
+    from paper_cs_0103001_gb300 import _native as nat
+
+    peak, _ = measured_peaks()
+    res = {}
+    for n in (1, 2, 4, 8):
+        x = img.expand(n, *img.shape).contiguous()
+        out = torch.empty_like(x)
+        plan = gb.Plan2D(img.shape[0], img.shape[1], n, img.device)
+        ms = _timed(lambda: plan.filter(x, H, out=out), steps, 5, flush)
+        plan.set_option(nat.OPT_PROFILE, 1)
+        for i in range(steps):
+            flush.fill_(i & 0xFF)
+            plan.filter(x, H, out=out)
+        torch.cuda.synchronize()
+        st = plan.profile_read()
+        plan.set_option(nat.OPT_PROFILE, 0)
+        us = ms * 1e3 / n
+        res[str(n)] = {"us_per_image": round(us, 1),
+                       "stage_us_per_image": {k: round(v[0] / v[1] * 1e3 / n, 2) for k, v in st.items()},
+                       "frac_algorithmic": round((26 + 6 / n) * img.numel() / (us * 1e-6) / 1e9 / peak, 3)}
+        del plan, x, out
+        torch.cuda.empty_cache()
+    return res
 
 
 def variant_paper_application(steps: int = 200):

@@ -226,10 +226,12 @@ __global__ void __launch_bounds__(ColCfg<N>::THREADS, BL)
     uint64_t *bar = reinterpret_cast<uint64_t *>(base + 2 * K::BUF + 2 * K::FB);
     const long long hmask = (1LL << log2half) - 1;
     const int t = threadIdx.x;
+    pdl_release();  // the inverse row pass may launch and wait for this one
     if (t == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
     }
+    pdl_wait();  // the forward row pass's spectra are complete
     __syncthreads();
     long long c = blockIdx.x;
     if (t == 0 && c < ncols) {  // the first column and its filter into buffer 0
@@ -305,11 +307,11 @@ static cudaError_t run_cols_tma(void *spec, const float *hs, const float *beta, 
     const long long rounds = (ncols + slots - 1) / slots;
     const long long grid = (ncols + rounds - 1) / rounds;  // the fewest blocks for the same number of rounds
     const int log2half = cs.ls ? ilog2(cs.mloc) : ilog2(cols / 2);
-    kern<<<(unsigned)grid, K::THREADS, K::SMEM, s>>>(map, hs, beta, hs_img, beta_img, log2half, ncols, log2g,
-                                                     static_cast<const float2 *>(tw), status, crows, boxr, cstride,
-                                                     nchunk, cs.kbase);
-    *used = true;
-    return cudaGetLastError();
+    cudaError_t e = launch_pdl(kern, dim3((unsigned)grid), dim3(K::THREADS), K::SMEM, s, map, hs, beta, hs_img,
+                               beta_img, log2half, ncols, log2g, static_cast<const float2 *>(tw), status, crows,
+                               boxr, cstride, nchunk, cs.kbase);
+    *used = e == cudaSuccess;
+    return e;
 }
 
 // form: 0 = the default (the TMA-fed persistent kernel with its filter in

@@ -128,6 +128,7 @@ __global__ void __launch_bounds__(RowCfg<M>::THREADS, RowCfg<M>::THREADS <= 512 
                    ImgIndirect ind) {
     extern __shared__ __align__(1024) unsigned char smraw[];
     unsigned char *base = smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u);  // the box's swizzle period
+    pdl_release();  // the column pass may launch and wait for this one
     const size_t y = blockIdx.y;
     const float *im = ind.ptrs ? ind.ptrs[ind.idx[y]].img : img + y * N * M;
     rows_fwd_body<M, Fp32Fft, false, true>(im, spec + y * (M / 2) * N, N, log2g, tw, blockIdx.x, base, Fp32Fft(),
@@ -188,6 +189,7 @@ __global__ void __launch_bounds__(RowCfg<M>::THREADS, 2)
     extern __shared__ __align__(1024) unsigned char smraw[];
     unsigned char *base = smraw + ((1024u - (smem_u32(smraw) & 1023u)) & 1023u);  // the box's swizzle period
     uint64_t *bar = reinterpret_cast<uint64_t *>(base + RowCfg<M>::SMEM);
+    pdl_wait();  // the column pass's spectra are complete
     const size_t y = blockIdx.y;
     float *o = ind.ptrs ? ind.ptrs[ind.idx[y]].out : out + y * N * M;
     rows_inv_body<M, Fp32Fft, false, true>(nullptr, o, N, log2g, tw, blockIdx.x, base, Fp32Fft(), Crop{0, 0}, &imap,
@@ -208,9 +210,8 @@ static cudaError_t run_rows_inv(const void *spec, float *out, int rows, int nimg
             cudaError_t e = set_smem<M>((const void *)k_rows_inv_tma<M>, smem);
             if (e != cudaSuccess) return e;
             dim3 grid((ld / 2) >> lg, nimg);
-            k_rows_inv_tma<M><<<grid, K::THREADS, smem, s>>>(out, rows, lg, static_cast<const float2 *>(tw), map,
-                                                             status, slab, ind);
-            return cudaGetLastError();
+            return launch_pdl(k_rows_inv_tma<M>, grid, dim3(K::THREADS), smem, s, out, rows, lg,
+                              static_cast<const float2 *>(tw), map, status, slab, ind);
         }
     }
     cudaError_t e = set_smem<M>((const void *)k_rows_inv<M>, K::SMEM);

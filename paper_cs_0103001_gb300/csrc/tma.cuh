@@ -100,6 +100,30 @@ __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.comm
 // until the issued stores have read their shared memory (it may be released then)
 __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
 
+// Programmatic dependent launch: a kernel launched with launch_pdl may start
+// while the previous kernel of its stream is still running (its blocks take
+// the SMs that kernel's last blocks leave free); before it reads anything
+// that kernel wrote, it calls pdl_wait(), which returns once that kernel has
+// completed and its memory is visible (at once for a plain launch).  A
+// kernel calls pdl_release() to let the next one launch early.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
+template <typename Kern, typename... Args>
+inline cudaError_t launch_pdl(Kern kern, dim3 grid, dim3 block, size_t smem, cudaStream_t s, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // Tests of a bounded wait (each followed by a 64 ns sleep): the copies of one
 // tile take microseconds, so a wait this long (about a quarter second or
 // more) means they will not complete.
