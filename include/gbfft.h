@@ -138,7 +138,10 @@ typedef enum {
     GBFFT_OPT_BATCH_FORM = 11
 } gbfft_option;
 
-/* Stages reported by gbfft_plan_profile_read. */
+/* Stages reported by gbfft_plan_profile_read.  With the environment
+ * variable GBFFT_NVTX=1 every stage launch is also wrapped in an NVTX range
+ * named "gbfft <stage>" (fft1d, fourstep_a, ..., as below) for a profiler's
+ * timeline. */
 typedef enum {
     GBFFT_STAGE_FFT1D = 0,     /* one-pass batched 1D transform */
     GBFFT_STAGE_FOURSTEP_A = 1,/* four-step pass A (column FFTs + twiddle) */
@@ -416,6 +419,23 @@ int gbfft_checked_take(int64_t *first_site, int64_t *failures);
  * next gbfft_device_status returns GBFFT_ERR_TIMEOUT.  Needs a bound
  * workspace; GBFFT_ERR_INVALID_VALUE for polls out of range. */
 int gbfft_selftest_wait_timeout(gbfft_plan_t plan, int64_t polls, gbfft_stream_t stream);
+
+/* Fault injection on the host, for tests of the failure paths (no GPU
+ * fault is ever made):
+ * gbfft_selftest_corrupt_work_item overwrites work item `index` of stage
+ * `stage` (0 forward rows, 1 columns, 2 inverse rows, 3 filter preparation)
+ * of a batched plan's host tables with (img, bx) and marks the plan unbound;
+ * fft_plan_bind_workspace checks every item against its image's launch shape
+ * before anything reaches the GPU and returns GBFFT_ERR_INVALID_VALUE for an
+ * item out of range (GBFFT_ERR_INVALID_VALUE here for a plan that is not
+ * batched or an index out of range).
+ * gbfft_selftest_launch_config makes a launch the CUDA runtime refuses
+ * (a block of 2048 threads) on `stream` and returns its status:
+ * GBFFT_ERR_CUDA, with gbfft_last_cuda_error() the runtime's refusal code
+ * (cudaErrorInvalidValue under CUDA 13); the refusal leaves the context
+ * usable. */
+int gbfft_selftest_corrupt_work_item(gbfft_plan_t plan, int stage, int64_t index, int img, int bx);
+int gbfft_selftest_launch_config(gbfft_stream_t stream);
 
 /* Diagnostic (the paper has no counterpart): measures the GPU's FMA
  * throughput, fp64 = 1 in double precision (the ALU roofline of the

@@ -73,6 +73,8 @@ SIGNATURES = {
     "gbfft_plan_check_guards": (_INT, [_P, ctypes.POINTER(ctypes.c_int64)]),
     "gbfft_checked_take": (_INT, [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)]),
     "gbfft_selftest_wait_timeout": (_INT, [_P, _I64, _P]),
+    "gbfft_selftest_corrupt_work_item": (_INT, [_P, _INT, _I64, _INT, _INT]),
+    "gbfft_selftest_launch_config": (_INT, [_P]),
     "fft2_filter_ifft2_backward": (_INT, [_P, _P, _P, _P, _P, _P, _P]),
     "fft_plan_destroy": (_INT, [_P]),
     "fft2_batched_plan_create": (_INT, [_INT, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_P)]),

@@ -9,7 +9,10 @@
 #include <vector>
 
 #include <cstdio>
+#include <cstdlib>
 #include <string>
+
+#include <nvtx3/nvToolsExt.h>
 
 #include "batched.h"
 #include "check.cuh"
@@ -269,6 +272,23 @@ bool misaligned(const void *ptr) { return (reinterpret_cast<uintptr_t>(ptr) & 15
 // Launch wrapper that records a profiling event pair when enabled.
 template <typename F>
 int launch(gbfft_plan *p, int stage, cudaStream_t s, F &&f) {
+    // NVTX range per stage launch (GBFFT_NVTX=1; a profiler such as Nsight
+    // Systems shows them on the host thread beside the kernels they issue)
+    static const bool nvtx = [] {
+        const char *v = getenv("GBFFT_NVTX");
+        return v && v[0] && v[0] != '0';
+    }();
+    static const char *const names[GBFFT_STAGE_COUNT] = {
+        "gbfft fft1d",  "gbfft fourstep_a", "gbfft fourstep_b",  "gbfft rows_fwd", "gbfft cols_filter",
+        "gbfft rows_inv", "gbfft cols_grad", "gbfft twiddles",   "gbfft graph",    "gbfft filter_prep",
+        "gbfft onchip", "gbfft spectrum",   "gbfft fft1d_cluster"};
+    if (nvtx) nvtxRangePushA(stage >= 0 && stage < GBFFT_STAGE_COUNT ? names[stage] : "gbfft");
+    struct Pop {
+        bool on;
+        ~Pop() {
+            if (on) nvtxRangePop();
+        }
+    } pop{nvtx};
     cudaEvent_t a = nullptr, b = nullptr;
     if (p->opt_profile) {
         if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) {
@@ -568,10 +588,41 @@ int fft_plan_workspace_bytes(gbfft_plan_t p, size_t *bytes) {
     return GBFFT_OK;
 }
 
+// The batched kernels index images and blocks through the plan's tables
+// without checks: every work item must lie inside its image's launch shape
+// and every class member must be an image of that shape.  Host only.
+int check_batch_tables(const gbfft_plan *p) {
+    const int n = (int)p->bimgs.size();
+    for (int st = 0; st < kBatchStages; ++st)
+        for (const BatchItem &it : p->bitems[st]) {
+            if (it.img < 0 || it.img >= n || it.bx < 0) return GBFFT_ERR_INVALID_VALUE;
+            const BatchImage &im = p->bimgs[it.img];
+            int blocks;
+            if (st == 0 || st == 2) {
+                blocks = (im.rows / 2) >> im.log2g;
+            } else if (st == 1) {
+                const int w = batch_col_width(im.rows);
+                blocks = (im.cols / 2 + w - 1) / w;
+            } else {
+                blocks = batch_prep_tiles(im.rows, im.cols);
+            }
+            if (it.bx >= blocks) return GBFFT_ERR_INVALID_VALUE;
+        }
+    for (const auto &c : p->bclasses)
+        for (int i : c.imgs)
+            if (i < 0 || i >= n || p->bimgs[i].rows != c.rows || p->bimgs[i].cols != c.cols)
+                return GBFFT_ERR_INVALID_VALUE;
+    return GBFFT_OK;
+}
+
 int fft_plan_bind_workspace(gbfft_plan_t p, void *workspace, size_t bytes, gbfft_stream_t stream) {
     if (!p || !workspace) return GBFFT_ERR_NULL;
     if ((reinterpret_cast<uintptr_t>(workspace) & (kAlign - 1)) != 0) return GBFFT_ERR_MISALIGNED;
     if (bytes < p->need) return GBFFT_ERR_WORKSPACE;
+    if (p->kind == KIND_BATCH) {  // before anything reaches the GPU
+        const int rc = check_batch_tables(p);
+        if (rc) return rc;
+    }
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     p->ws = static_cast<char *>(workspace);
     p->ws_bytes = bytes;
@@ -1459,6 +1510,21 @@ int gbfft_selftest_wait_timeout(gbfft_plan_t p, int64_t polls, gbfft_stream_t st
     if (polls < 1 || polls > (int64_t)kTmaPolls) return GBFFT_ERR_INVALID_VALUE;
     cudaError_t e = launch_wait_timeout(reinterpret_cast<int *>(p->ws + p->off_status), (unsigned)polls,
                                         static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? GBFFT_OK : cuda_fail(e);
+}
+
+int gbfft_selftest_corrupt_work_item(gbfft_plan_t p, int stage, int64_t index, int img, int bx) {
+    if (!p) return GBFFT_ERR_NULL;
+    if (p->kind != KIND_BATCH || stage < 0 || stage >= kBatchStages || index < 0 ||
+        index >= (int64_t)p->bitems[stage].size())
+        return GBFFT_ERR_INVALID_VALUE;
+    p->bitems[stage][index] = BatchItem{img, bx};
+    p->bound = false;  // the device copy no longer matches: the plan must be bound again
+    return GBFFT_OK;
+}
+
+int gbfft_selftest_launch_config(gbfft_stream_t stream) {
+    const cudaError_t e = launch_bad_config(static_cast<cudaStream_t>(stream));
     return e == cudaSuccess ? GBFFT_OK : cuda_fail(e);
 }
 

@@ -40,6 +40,9 @@ cudaError_t launch_fourstep_full_twiddles(void *tw, int n, int log2n2, cudaStrea
 // One block whose bounded mbarrier wait cannot succeed: sets *status after
 // `polls` tests (selftest.cu).
 cudaError_t launch_wait_timeout(int *status, unsigned polls, cudaStream_t s);
+// A launch the runtime refuses before it reaches the GPU (a block of 2048
+// threads; the refusal does not poison the context).
+cudaError_t launch_bad_config(cudaStream_t s);
 // Index-bound check words of the GBFFT_CHECKED build (check.cuh), one per
 // translation unit that checks: read and clear (synchronous).
 cudaError_t check_take_rows(unsigned out[2]);

@@ -25,6 +25,13 @@ cudaError_t launch_wait_timeout(int *status, unsigned polls, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+__global__ void k_never_runs() {}
+
+cudaError_t launch_bad_config(cudaStream_t s) {
+    k_never_runs<<<1, 2048, 0, s>>>();  // more threads than a block may have: refused at launch
+    return cudaGetLastError();          // reads and clears the launch error
+}
+
 // Guard bands of a plan's workspace (api.cu): kAlign = 256 bytes after every
 // region, filled with a fixed word at bind and checked on request.  The
 // offsets come from a table in the workspace; an offset outside the

@@ -158,3 +158,32 @@ def test_slab_plan_validation_without_gpu(nat):
     assert nat.lib.fft2_slab_columns(h, buf, buf, None) == nat.ERR_WORKSPACE
     assert nat.lib.fft2_slab_rows_inverse(h, buf, buf, None) == nat.ERR_WORKSPACE
     assert nat.lib.fft_plan_destroy(h) == nat.OK
+
+
+def test_corrupted_work_list_is_refused_before_the_gpu(nat):
+    """A batched plan's work items index images and blocks unchecked on the
+    GPU; binding checks every item on the host first.  A corrupted item
+    (image or block out of range) makes the bind return
+    GBFFT_ERR_INVALID_VALUE without a CUDA call (this test has no GPU)."""
+    shapes = [(64, 128), (256, 256), (1024, 512)]
+    rows = (ctypes.c_int64 * 3)(*[r for r, _ in shapes])
+    cols = (ctypes.c_int64 * 3)(*[c for _, c in shapes])
+    ws = ctypes.c_size_t()
+    fake = ctypes.c_void_p(1 << 20)  # aligned, never dereferenced: the bind stops before CUDA
+    for stage, img, bx in [(0, 3, 0), (1, -1, 0), (2, 0, 1 << 20), (3, 2, -5), (0, 0, 32)]:
+        h = ctypes.c_void_p()
+        assert nat.lib.fft2_batched_plan_create(3, rows, cols, ctypes.byref(h)) == nat.OK
+        assert nat.lib.fft_plan_workspace_bytes(h, ctypes.byref(ws)) == nat.OK
+        assert nat.lib.gbfft_selftest_corrupt_work_item(h, stage, 0, img, bx) == nat.OK
+        assert nat.lib.fft_plan_bind_workspace(h, fake, ws.value, None) == nat.ERR_INVALID_VALUE
+        # unbound: the pipeline refuses too
+        assert nat.lib.fft2_filter_ifft2_batched(h, fake, None) == nat.ERR_WORKSPACE
+        assert nat.lib.fft_plan_destroy(h) == nat.OK
+    h = ctypes.c_void_p()
+    assert nat.lib.fft2_batched_plan_create(3, rows, cols, ctypes.byref(h)) == nat.OK
+    assert nat.lib.gbfft_selftest_corrupt_work_item(h, 4, 0, 0, 0) == nat.ERR_INVALID_VALUE
+    assert nat.lib.gbfft_selftest_corrupt_work_item(h, 0, 1 << 30, 0, 0) == nat.ERR_INVALID_VALUE
+    assert nat.lib.fft_plan_destroy(h) == nat.OK
+    assert nat.lib.fft_plan_create(1024, 4, 1, ctypes.byref(h)) == nat.OK
+    assert nat.lib.gbfft_selftest_corrupt_work_item(h, 0, 0, 0, 0) == nat.ERR_INVALID_VALUE
+    assert nat.lib.fft_plan_destroy(h) == nat.OK
