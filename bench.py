@@ -406,6 +406,10 @@ def run_gbfft(args):
                     "note": "pct_hbm_peak = frac_algorithmic; frac_dram uses the ncu DRAM bytes of each stage "
                             "(profiles/dram_traffic.txt, null once a kernel changed since its capture)"},
             "us_per_image": round(ms * 1e3, 2),
+            "ms_p10": round(float(np.percentile(step_ms, 10)), 5),
+            "ms_p90": round(float(np.percentile(step_ms, 90)), 5),
+            "gpu": torch.cuda.get_device_name(dev),
+            "seed": {"image": [3, rank], "recipe": "synth.sky(4096, 4096, 20000, 3, rank)"},
             "images_per_s": round(world * 1e3 / ms, 1),
             "gflops_5nlogn": round(world * FLOPS_PER_IMAGE / (ms * 1e-3) / 1e9, 1),
             "value_bytes_per_px": METRIC_BYTES_PER_PX,
@@ -856,9 +860,19 @@ def main():
                     help="headline only, without the other workloads")
     ap.add_argument("--no-tune", dest="tune", action="store_false",
                     help="headline plan with its default configuration (no autotuner launches, e.g. under ncu)")
+    ap.add_argument("--log", default="",
+                    help="also append the JSON line to this file (one record per run, JSON lines)")
     args = ap.parse_args()
+
+    def emit(res):
+        line = json.dumps(res)
+        print(line, flush=True)
+        if args.log:
+            with open(args.log, "a") as f:
+                f.write(line + "\n")
+
     if args.impl == "gbfft" and args.workload != "pipeline4096":
-        print(json.dumps(run_workload(args)), flush=True)
+        emit(run_workload(args))
         return
     if args.warmup < 3 and args.impl == "gbfft":
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -870,7 +884,7 @@ def main():
         __graft_entry__._build_module().build()
         res = run_gbfft(args)
     if res is not None:
-        print(json.dumps(res), flush=True)
+        emit(res)
 
 
 if __name__ == "__main__":
