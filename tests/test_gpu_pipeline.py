@@ -151,3 +151,29 @@ def test_column_pass_forms(gb, form, rows, cols, batch):
     plan = gb.Plan2D(rows, cols, batch, "cuda", {nat.OPT_H_BATCH_STRIDE: rows * cols, nat.OPT_COLUMN_FORM: form})
     out = plan.filter(torch.from_numpy(img).cuda(), torch.from_numpy(H).cuda()).cpu().numpy()
     assert max_rel_l2(out, oracle.pipeline(img, H), axes=(1, 2)) <= tol_fp32(rows * cols)
+
+
+@pytest.mark.parametrize("per_image,chunk", [(True, 1), (True, 0), (False, 1), (False, 0)])
+def test_4096_filters_per_image_and_shared_over_chunks(gb, per_image, chunk):
+    """4096^2 images with asymmetric filters (the mirror terms of the
+    prepared filter matter): per-image filters, or one filter shared by every
+    image (prepared once per call, by the first chunk), one or all images per
+    chunk.  Column forms 1 and 2 read the same prepared filter from shared or
+    global memory with the same arithmetic, so they agree bit for bit; both
+    match the oracle."""
+    import torch
+
+    from paper_cs_0103001_gb300 import _native as nat
+
+    rows = cols = 4096
+    B = 3 if per_image else 2
+    img = np.stack([synth.sky(rows, cols, 3000, 18, b) for b in range(B)])
+    H = (np.stack([synth.random_filter(rows, cols, 19, b) for b in range(B)]) if per_image
+         else synth.random_filter(rows, cols, 19, 7))
+    opts = {nat.OPT_H_BATCH_STRIDE: rows * cols if per_image else 0, nat.OPT_IMAGES_PER_CHUNK: chunk}
+    ti, th = torch.from_numpy(img).cuda(), torch.from_numpy(H).cuda()
+    smem = gb.Plan2D(rows, cols, B, "cuda", {**opts, nat.OPT_COLUMN_FORM: 1}).filter(ti, th)
+    glob = gb.Plan2D(rows, cols, B, "cuda", {**opts, nat.OPT_COLUMN_FORM: 2}).filter(ti, th)
+    assert torch.equal(smem, glob)
+    ref = oracle.pipeline(img, H)
+    assert max_rel_l2(smem.cpu().numpy(), ref, axes=(1, 2)) <= tol_fp32(rows * cols)
