@@ -135,7 +135,15 @@ typedef enum {
      * the filter preparations and the small classes' on-chip pipelines on a
      * side stream; 1 = four persistent launches over largest-first work
      * lists of every image (GBFFT_OPT_BLOCKS_PER_SM applies).  Same results. */
-    GBFFT_OPT_BATCH_FORM = 11
+    GBFFT_OPT_BATCH_FORM = 11,
+    /* 1D complex64 plans of length 2^24: 3 (default, 0) = three passes of
+     * length-256 transforms (N = 256^3: two column passes, the second in
+     * place, and one row pass with transposed stores), each moving tiles of
+     * 32 transforms (256-byte runs in HBM); 2 = the two passes of 4096 of
+     * every other length, whose tiles hold 4 transforms (32-byte runs).  The
+     * workspace changes: query fft_plan_workspace_bytes and bind again.
+     * Same results up to rounding order. */
+    GBFFT_OPT_FOURSTEP_PASSES = 12
 } gbfft_option;
 
 /* Stages reported by gbfft_plan_profile_read.  With the environment

@@ -43,6 +43,7 @@ OPT_USE_GRAPH = 8
 OPT_ONCHIP = 9
 OPT_COLUMN_FORM = 10
 OPT_BATCH_FORM = 11
+OPT_FOURSTEP_PASSES = 12
 
 # gbfft_filter_kind
 FILTER_GAUSSIAN = 1

@@ -65,6 +65,8 @@ struct gbfft_plan {
     int64_t chunk = 0;           // transforms (1D four-step) or images (2D) per workspace chunk
     int nranks = 1, rank = 0;    // slab plans: the decomposition and this rank
     int fs_l1 = 0, fs_l2 = 0;    // four-step split
+    bool fs3 = false;            // three passes of 256 (complex64, N = 2^24)
+    size_t off_tw6 = 0, off_tw7 = 0;  // three passes: the middle pass's two-level and coarse tables
     std::vector<ProfRec> prof;
     // guard bands: kAlign bytes of a fixed pattern after every workspace
     // region (offsets here, and as a table in the workspace for the kernels
@@ -81,6 +83,7 @@ struct gbfft_plan {
     int64_t opt_graph = 1;
     int64_t opt_onchip = 1;
     int64_t opt_colform = 0;  // column-pass form (GBFFT_OPT_COLUMN_FORM)
+    int64_t opt_passes = 0;   // 1D complex64 2^24: two or three passes (GBFFT_OPT_FOURSTEP_PASSES)
     cudaStream_t cap_stream = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
@@ -170,6 +173,12 @@ void layout_batched(gbfft_plan *p) {
 }
 
 // Compute the workspace layout for the current options.
+// Three passes of 256 (complex64, N = 2^24, GBFFT_OPT_FOURSTEP_PASSES 3 or
+// default): see launch_fourstep_a_split in internal.h.
+bool fourstep3_applies(const gbfft_plan *p) {
+    return p->kind == KIND_1D && !is_dbl(p) && p->log2n == 24 && p->opt_passes != 2;
+}
+
 void layout(gbfft_plan *p) {
     size_t off = kAlign;  // a guard band before the first region
     p->guards.assign(1, 0);
@@ -193,11 +202,38 @@ void layout(gbfft_plan *p) {
     }
     if (p->kind == KIND_1D) {
         const int64_t n = int64_t(1) << p->log2n;
+        p->fs3 = false;
         if (p->log2n <= max_single_log2(p)) {
             p->off_tw0 = off;
             off = region_end(p, off + (size_t)n * csize(p));
             p->off_tw1 = p->off_tw2 = p->off_buf = off;
             p->chunk = p->batch;
+        } else if (fourstep3_applies(p)) {
+            // three passes of 256: one Stockham table (length 256), the first
+            // pass's two-level (N) and coarse (16 x 2^16) tables, the middle
+            // pass's two-level (2^16) and coarse (16 x 256) tables
+            p->fs3 = true;
+            p->fs_l1 = 8;
+            p->fs_l2 = 16;
+            const int lf = (p->log2n + 1) / 2;
+            p->off_tw0 = p->off_tw1 = off;
+            off = region_end(p, off + (size_t)256 * 8);
+            p->off_tw2 = off;
+            off = region_end(p, off + (size_t)((int64_t(1) << lf) + (n >> lf)) * 8);
+            p->off_tw5 = off;
+            off = region_end(p, off + (size_t)16 * 65536 * 8);
+            p->off_tw6 = off;
+            off = region_end(p, off + (size_t)(256 + 256) * 8);
+            p->off_tw7 = off;
+            off = region_end(p, off + (size_t)16 * 256 * 8);
+            p->off_tw3 = off;
+            p->off_buf = off;
+            int64_t chunk = p->opt_chunk;
+            if (chunk <= 0) chunk = kFourStepChunkBytes / (n * 8);
+            if (chunk < 1) chunk = 1;
+            if (chunk > p->batch) chunk = p->batch;
+            p->chunk = chunk;
+            off = region_end(p, off + (size_t)chunk * n * 8);
         } else {
             fourstep_split(p->log2n, is_dbl(p), &p->fs_l1, &p->fs_l2);
             const int64_t n1 = int64_t(1) << p->fs_l1, n2 = int64_t(1) << p->fs_l2;
@@ -333,6 +369,30 @@ int run_1d(gbfft_plan *p, const void *in, void *out, int dir, cudaStream_t s) {
         });
     }
     const size_t cs = csize(p);
+    if (p->fs3) {
+        int *status = reinterpret_cast<int *>(p->ws + p->off_status);
+        void *tmp = p->ws + p->off_buf;
+        for (int64_t b0 = 0; b0 < p->batch; b0 += p->chunk) {
+            const int64_t nb = (p->batch - b0 < p->chunk) ? p->batch - b0 : p->chunk;
+            const char *src = static_cast<const char *>(in) + (size_t)b0 * n * cs;
+            char *dst = static_cast<char *>(out) + (size_t)b0 * n * cs;
+            rc = launch(p, GBFFT_STAGE_FOURSTEP_A, s, [&] {
+                return launch_fourstep_a_split(src, tmp, 8, 16, nb, dir, p->ws + p->off_tw0, p->ws + p->off_tw2,
+                                               p->ws + p->off_tw5, status, s);
+            });
+            if (rc) return rc;
+            rc = launch(p, GBFFT_STAGE_FOURSTEP_A, s, [&] {
+                return launch_fourstep_a_split(tmp, tmp, 8, 8, nb * 256, dir, p->ws + p->off_tw0, p->ws + p->off_tw6,
+                                               p->ws + p->off_tw7, status, s);
+            });
+            if (rc) return rc;
+            rc = launch(p, GBFFT_STAGE_FOURSTEP_B, s, [&] {
+                return launch_fourstep_b_split(tmp, dst, 16, 8, 8, nb, dir, p->ws + p->off_tw0, scale, status, s);
+            });
+            if (rc) return rc;
+        }
+        return GBFFT_OK;
+    }
     for (int64_t b0 = 0; b0 < p->batch; b0 += p->chunk) {
         const int64_t nb = (p->batch - b0 < p->chunk) ? p->batch - b0 : p->chunk;
         const char *src = static_cast<const char *>(in) + (size_t)b0 * n * cs;
@@ -578,6 +638,12 @@ int fft_plan_set_option(gbfft_plan_t p, int key, int64_t value) {
             if ((p->kind != KIND_2D && p->kind != KIND_SLAB) || value < 0 || value > 3) return GBFFT_ERR_INVALID_VALUE;
             p->opt_colform = value;
             return GBFFT_OK;
+        case GBFFT_OPT_FOURSTEP_PASSES:
+            if (p->kind != KIND_1D || (value != 0 && value != 2 && value != 3)) return GBFFT_ERR_INVALID_VALUE;
+            p->opt_passes = value;
+            layout(p);
+            p->bound = false;  // the workspace's regions moved: bind again
+            return GBFFT_OK;
         default: return GBFFT_ERR_INVALID_VALUE;
     }
 }
@@ -644,6 +710,15 @@ int fft_plan_bind_workspace(gbfft_plan_t p, void *workspace, size_t bytes, gbfft
     if (p->kind == KIND_1D) {
         if (p->log2n <= max_single_log2(p)) {
             rc = launch(p, GBFFT_STAGE_TWIDDLES, s, [&] { return launch_twiddles(p->ws + p->off_tw0, 1 << p->log2n, dbl, s); });
+        } else if (p->fs3) {
+            rc = launch(p, GBFFT_STAGE_TWIDDLES, s, [&] {
+                cudaError_t e = launch_twiddles(p->ws + p->off_tw0, 256, false, s);
+                if (e == cudaSuccess) e = launch_fourstep_twiddles(p->ws + p->off_tw2, 1 << p->log2n, false, s);
+                if (e == cudaSuccess) e = launch_fourstep_coarse_twiddles(p->ws + p->off_tw5, 65536, false, s);
+                if (e == cudaSuccess) e = launch_fourstep_twiddles(p->ws + p->off_tw6, 65536, false, s);
+                if (e == cudaSuccess) e = launch_fourstep_coarse_twiddles(p->ws + p->off_tw7, 256, false, s);
+                return e;
+            });
         } else {
             rc = launch(p, GBFFT_STAGE_TWIDDLES, s, [&] {
                 cudaError_t e = launch_twiddles(p->ws + p->off_tw0, 1 << p->fs_l1, dbl, s);
@@ -1455,6 +1530,7 @@ int fft_plan_get_option(gbfft_plan_t p, int key, int64_t *value) {
         case GBFFT_OPT_ONCHIP: *value = p->opt_onchip; return GBFFT_OK;
         case GBFFT_OPT_COLUMN_FORM: *value = p->opt_colform; return GBFFT_OK;
         case GBFFT_OPT_BATCH_FORM: *value = p->opt_batch_form; return GBFFT_OK;
+        case GBFFT_OPT_FOURSTEP_PASSES: *value = p->fs3 ? 3 : 2; return GBFFT_OK;
         default: return GBFFT_ERR_INVALID_VALUE;
     }
 }

@@ -72,6 +72,15 @@ __device__ __forceinline__ C tw_two_level(const C *__restrict__ t4, int idx, int
     return cmul(hi, lo);
 }
 
+// Row k1 of pass B's input: row k1 itself (log2p = 0), or, for the last
+// pass of a three-pass split, row (k1 mod P) (n1 / P) + k1 / P (P = 2^log2p):
+// the middle pass leaves its rows in the order [k1'][k2'] with k1' < P, and
+// the output index wants k1 = k1' + P k2'.
+__device__ __forceinline__ size_t perm_row(int k1, int log2n1, int log2p) {
+    if (log2p == 0) return (size_t)k1;
+    return ((size_t)(k1 & ((1 << log2p) - 1)) << (log2n1 - log2p)) + (size_t)(k1 >> log2p);
+}
+
 // Pass A: column transforms of length N1 (= N) over the N1 x n2 view.
 template <int N, int DIR, typename R>
 __global__ void __launch_bounds__(FsCfg<N, R>::MAXT, FsCfg<N, R>::MINB)
@@ -180,7 +189,7 @@ __global__ void __launch_bounds__(FsCfg<N, float>::MAXT, FsCfg<N, float>::MINB)
 template <int N, int DIR, typename R>
 __global__ void __launch_bounds__(FsCfg<N, R>::MAXT, FsCfg<N, R>::MINB)
     k_fourstep_b(const typename cvec<R>::type *tmp, typename cvec<R>::type *out, int log2n1,
-                 const typename cvec<R>::type *__restrict__ tw, R scale) {
+                 const typename cvec<R>::type *__restrict__ tw, R scale, int log2p) {
     typedef typename cvec<R>::type C;
     typedef FsCfg<N, R> K;
     constexpr int E = K::E, T = K::T, W = K::WMAX;
@@ -190,7 +199,7 @@ __global__ void __launch_bounds__(FsCfg<N, R>::MAXT, FsCfg<N, R>::MINB)
     const int t = threadIdx.x / W;
     const int k1 = blockIdx.x * W + w;
     const size_t img = (size_t)blockIdx.y * ((size_t)N << log2n1);
-    const C *row = tmp + img + (size_t)k1 * N;
+    const C *row = tmp + img + (size_t)perm_row(k1, log2n1, log2p) * N;
     C v[E];
 #pragma unroll
     for (int e = 0; e < E; ++e) v[e] = row[t + T * e];
@@ -210,7 +219,7 @@ __global__ void __launch_bounds__(FsCfg<N, R>::MAXT, FsCfg<N, R>::MINB)
 template <int N, int DIR>
 __global__ void __launch_bounds__(FsCfg<N, float>::MAXT, FsCfg<N, float>::MINB)
     k_fourstep_b_tma(const float2 *tmp, const __grid_constant__ CUtensorMap omap, int log2n1,
-                     const float2 *__restrict__ tw, float scale, int *status) {
+                     const float2 *__restrict__ tw, float scale, int *status, int log2p) {
     typedef FsCfg<N, float> K;
     constexpr int E = K::E, T = K::T, W = K::WMAX, BR = N < 256 ? N : 256, RP = N + 2;
     extern __shared__ __align__(128) unsigned char smraw[];
@@ -227,8 +236,9 @@ __global__ void __launch_bounds__(FsCfg<N, float>::MAXT, FsCfg<N, float>::MINB)
     __syncthreads();
     if (threadIdx.x == 0) {
         mbar_expect_tx(bar, (uint32_t)(N * W * sizeof(float2)));
-        const float2 *src = tmp + (size_t)blockIdx.y * ((size_t)N << log2n1) + (size_t)k10 * N;
-        for (int r = 0; r < W; ++r) bulk_load(sm + r * RP, src + (size_t)r * N, N * sizeof(float2), bar);
+        const float2 *src = tmp + (size_t)blockIdx.y * ((size_t)N << log2n1);
+        for (int r = 0; r < W; ++r)
+            bulk_load(sm + r * RP, src + (size_t)perm_row(k10 + r, log2n1, log2p) * N, N * sizeof(float2), bar);
         int done = mbar_wait_bounded(bar, 0, kTmaPolls) ? 1 : 0;
         if (!done) {
             atomicExch(status, 1);
@@ -322,7 +332,7 @@ static cudaError_t run_a(const void *in, void *tmp, int log2n2, long long nb, in
 
 template <int N, typename R>
 static cudaError_t run_b_tma(const void *tmp, void *out, int log2n1, long long nb, int dir, const void *tw,
-                             double scale, int *status, cudaStream_t s, bool *used) {
+                             double scale, int *status, cudaStream_t s, bool *used, int log2p) {
     *used = false;
     if constexpr (sizeof(R) != 4 || FsCfg<N, float>::MINB < 2) {
         // one block per SM: it would idle while its tensor stores drain
@@ -349,7 +359,7 @@ static cudaError_t run_b_tma(const void *tmp, void *out, int log2n1, long long n
         if (e != cudaSuccess) return e;
         dim3 grid((unsigned)(n1 / W), (unsigned)nb);
         kern<<<grid, W * K::T, smem, s>>>(static_cast<const float2 *>(tmp), map, log2n1,
-                                          static_cast<const float2 *>(tw), (float)scale, status);
+                                          static_cast<const float2 *>(tw), (float)scale, status, log2p);
         *used = true;
         return cudaGetLastError();
     }
@@ -357,10 +367,10 @@ static cudaError_t run_b_tma(const void *tmp, void *out, int log2n1, long long n
 
 template <int N, typename R>
 static cudaError_t run_b(const void *tmp, void *out, int log2n1, long long nb, int dir, const void *tw, double scale,
-                         int *status, cudaStream_t s) {
+                         int *status, cudaStream_t s, int log2p) {
     if (nb > 65535) return cudaErrorInvalidConfiguration;
     bool used = false;
-    cudaError_t te = run_b_tma<N, R>(tmp, out, log2n1, nb, dir, tw, scale, status, s, &used);
+    cudaError_t te = run_b_tma<N, R>(tmp, out, log2n1, nb, dir, tw, scale, status, s, &used, log2p);
     if (te != cudaSuccess || used) return te;
     typedef typename cvec<R>::type C;
     typedef FsCfg<N, R> K;
@@ -372,7 +382,7 @@ static cudaError_t run_b(const void *tmp, void *out, int log2n1, long long nb, i
     if (nb > 65535) return cudaErrorInvalidConfiguration;
     dim3 grid((1 << log2n1) / W, (unsigned)nb);
     kern<<<grid, W * K::T, smem, s>>>(static_cast<const C *>(tmp), static_cast<C *>(out), log2n1,
-                                      static_cast<const C *>(tw), (R)scale);
+                                      static_cast<const C *>(tw), (R)scale, log2p);
     return cudaGetLastError();
 }
 
@@ -393,10 +403,10 @@ static cudaError_t dispatch_a(const void *in, void *tmp, int l1, int l2, long lo
 
 template <typename R>
 static cudaError_t dispatch_b(const void *tmp, void *out, int l1, int l2, long long nb, int dir, const void *tw,
-                              double scale, int *status, cudaStream_t s) {
+                              double scale, int *status, cudaStream_t s, int log2p) {
     switch (l2) {
 #define GBFFT_B(L) \
-    case L: return run_b<(1 << L), R>(tmp, out, l1, nb, dir, tw, scale, status, s);
+    case L: return run_b<(1 << L), R>(tmp, out, l1, nb, dir, tw, scale, status, s, log2p);
         GBFFT_FS_CASES(GBFFT_B)
 #undef GBFFT_B
         default: return cudaErrorInvalidValue;
@@ -417,8 +427,20 @@ cudaError_t launch_fourstep_b(const void *tmp, void *out, int log2n, long long b
                               const void *tw_n2, double scale, int *status, cudaStream_t s) {
     int l1, l2;
     fourstep_split(log2n, dbl, &l1, &l2);
-    return dbl ? dispatch_b<double>(tmp, out, l1, l2, batch, dir, tw_n2, scale, status, s)
-               : dispatch_b<float>(tmp, out, l1, l2, batch, dir, tw_n2, scale, status, s);
+    return dbl ? dispatch_b<double>(tmp, out, l1, l2, batch, dir, tw_n2, scale, status, s, 0)
+               : dispatch_b<float>(tmp, out, l1, l2, batch, dir, tw_n2, scale, status, s, 0);
+}
+
+cudaError_t launch_fourstep_a_split(const void *in, void *tmp, int log2n1, int log2n2, long long batch, int dir,
+                                    const void *tw_n1, const void *tw_4s, const void *tw_coarse, int *status,
+                                    cudaStream_t s) {
+    const int log2f = (log2n1 + log2n2 + 1) / 2;
+    return dispatch_a<float>(in, tmp, log2n1, log2n2, batch, dir, tw_n1, tw_4s, log2f, tw_coarse, status, s);
+}
+
+cudaError_t launch_fourstep_b_split(const void *tmp, void *out, int log2n1, int log2n2, int log2p, long long batch,
+                                    int dir, const void *tw_n2, double scale, int *status, cudaStream_t s) {
+    return dispatch_b<float>(tmp, out, log2n1, log2n2, batch, dir, tw_n2, scale, status, s, log2p);
 }
 
 }  // namespace gbfft

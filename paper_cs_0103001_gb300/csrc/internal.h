@@ -75,6 +75,20 @@ cudaError_t launch_fourstep_a(const void *in, void *tmp, int log2n, long long ba
                               cudaStream_t s);
 cudaError_t launch_fourstep_b(const void *tmp, void *out, int log2n, long long batch, bool dbl, int dir,
                               const void *tw_n2, double scale, int *status, cudaStream_t s);
+// The same passes of complex64 with an explicit split n1 x n2 (the three-pass
+// schedule below): pass A with the two-level table of n1 n2 and the coarse
+// table of n2; pass B reading its row k1 from row (k1 mod 2^log2p) (n1 /
+// 2^log2p) + k1 / 2^log2p of tmp when log2p > 0.
+// Three passes for N = 2^24 = 256^3 (j = j1 2^16 + j2 256 + j3, k = k1 +
+// 256 k2 + 2^16 k3): pass A over the 256 x 2^16 view (W_N twiddles) into
+// tmp; pass A over each of its 256 rows as 256 x 256 (W_(2^16) twiddles) in
+// place; pass B over rows k1 + 256 k2 (stored at k1 256 + k2, log2p = 8) into
+// the output.  Every pass moves tiles of 32 transforms: 256-byte runs.
+cudaError_t launch_fourstep_a_split(const void *in, void *tmp, int log2n1, int log2n2, long long batch, int dir,
+                                    const void *tw_n1, const void *tw_4s, const void *tw_coarse, int *status,
+                                    cudaStream_t s);
+cudaError_t launch_fourstep_b_split(const void *tmp, void *out, int log2n1, int log2n2, int log2p, long long batch,
+                                    int dir, const void *tw_n2, double scale, int *status, cudaStream_t s);
 
 // 2D pipeline stages (float32 images).  Intermediate, per image: half spectra
 // [cols/2][rows] complex64, column-major in slot order (layout.cuh; column 0

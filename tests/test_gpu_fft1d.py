@@ -211,3 +211,24 @@ def test_bounded_wait_timeout_is_reported_and_the_plan_stays_usable(gb):
     with pytest.raises(nat.GbfftError) as err:
         plan.selftest_wait_timeout(0)  # out of range
     assert err.value.status == nat.ERR_INVALID_VALUE
+
+
+@pytest.mark.parametrize("passes", [2, 3])
+def test_two_and_three_pass_schedules_at_2_24(gb, passes):
+    """Length 2^24 (complex64) as two passes of 4096 or three passes of 256
+    (GBFFT_OPT_FOURSTEP_PASSES), forward and inverse against the oracle, with
+    batch 2 and one transform per workspace chunk (so the chunk loop runs)."""
+    import torch
+
+    from paper_cs_0103001_gb300 import _native as nat
+
+    n, batch = 1 << 24, 2
+    x = synth.complex_uniform((batch, n), 2, 24, passes)
+    plan = gb.Plan1D(n, batch, torch.complex64, "cuda", {nat.OPT_FOURSTEP_PASSES: passes,
+                                                         nat.OPT_IMAGES_PER_CHUNK: 1})
+    assert plan.get_option(nat.OPT_FOURSTEP_PASSES) == passes
+    t = torch.from_numpy(x).cuda()
+    xo = x.astype(np.complex128)
+    assert max_rel_l2(plan.forward(t).cpu().numpy(), oracle.fft(xo), axes=-1) <= _tol(n, False)
+    assert max_rel_l2(plan.inverse(t).cpu().numpy(), oracle.ifft(xo), axes=-1) <= _tol(n, False)
+    plan.device_status()
