@@ -370,70 +370,53 @@ __device__ __forceinline__ void filter_prep_tile(const float *__restrict__ hb, f
         // unit = (row r, four consecutive columns); the mirror run [M-k-3, M-k]
         // comes from two aligned quads (for k = 0 the element M - k is column 0)
         const int nq = K >> 2, units = R << (log2k - 2);
+        struct Unit {
+            float4 f, m1;  // H[u][k .. k+3] and H[-u][M-k-4 .. M-k-1]
+            float m0;      // H[-u][M-k] (H[-u][0] for k = 0)
+        };
+        auto load = [&](int q) {
+            const int r = q >> (log2k - 2), kq = (q & (nq - 1)) << 2;
+            const int u = u0 + r, mu = (N - u) & (N - 1);
+            const int k = k0 + kq;
+            const float *Hu = hb + (size_t)u * M, *Hm = hb + (size_t)mu * M;
+            Unit x;
+            x.f = __ldcs(reinterpret_cast<const float4 *>(Hu + k));
+            x.m1 = __ldcs(reinterpret_cast<const float4 *>(Hm + (M - k - 4)));
+            x.m0 = k == 0 ? Hm[0] : __ldcs(Hm + (M - k));
+            return x;
+        };
+        auto stage = [&](int q, const Unit &x) {
+            const int r = q >> (log2k - 2), kq = (q & (nq - 1)) << 2;
+            const int u = u0 + r, mu = (N - u) & (N - 1);
+            float v0;
+            if (k0 + kq == 0) {
+                const float h0 = 0.5f * (x.f.x + x.m0);
+                const float h1 = 0.5f * (hb[(size_t)u * M + H2] + hb[(size_t)mu * M + H2]);
+                v0 = hsc * (h0 + h1);
+                betaz[u] = hsc * (h0 - h1);
+            } else {
+                v0 = hsc * (x.f.x + x.m0);
+            }
+            float *tc = tile + kq * SR + r;
+            tc[0] = v0;
+            tc[SR] = hsc * (x.f.y + x.m1.w);
+            tc[2 * SR] = hsc * (x.f.z + x.m1.z);
+            tc[3 * SR] = hsc * (x.f.w + x.m1.y);
+        };
         // the usual tile (64 columns, 256 threads): U units per thread, every
         // load of the thread issued before the first is used (measured 4096^2
         // pipeline 133.0 -> 132.4 us: the preparation shares the SMs with the
         // forward row pass, so its blocks should not wait on one load at a time)
         constexpr int U = R / 16;
         if (U >= 1 && units == U * (int)blockDim.x) {
-            float4 fv[U >= 1 ? U : 1], mv[U >= 1 ? U : 1];
-            float m0v[U >= 1 ? U : 1];
+            Unit x[U >= 1 ? U : 1];
 #pragma unroll
-            for (int i = 0; i < U; ++i) {
-                const int q = threadIdx.x + i * blockDim.x;
-                const int r = q >> (log2k - 2), kq = (q & (nq - 1)) << 2;
-                const int u = u0 + r, mu = (N - u) & (N - 1);
-                const int k = k0 + kq;
-                const float *Hu = hb + (size_t)u * M, *Hm = hb + (size_t)mu * M;
-                fv[i] = __ldcs(reinterpret_cast<const float4 *>(Hu + k));
-                mv[i] = __ldcs(reinterpret_cast<const float4 *>(Hm + (M - k - 4)));
-                m0v[i] = k == 0 ? Hm[0] : __ldcs(Hm + (M - k));
-            }
+            for (int i = 0; i < U; ++i) x[i] = load(threadIdx.x + i * blockDim.x);
 #pragma unroll
-            for (int i = 0; i < U; ++i) {
-                const int q = threadIdx.x + i * blockDim.x;
-                const int r = q >> (log2k - 2), kq = (q & (nq - 1)) << 2;
-                const int u = u0 + r, mu = (N - u) & (N - 1);
-                const int k = k0 + kq;
-                const float4 f = fv[i], m1 = mv[i];
-                float v0;
-                if (k == 0) {
-                    const float *Hu = hb + (size_t)u * M, *Hm = hb + (size_t)mu * M;
-                    const float h0 = 0.5f * (f.x + m0v[i]), h1 = 0.5f * (Hu[H2] + Hm[H2]);
-                    v0 = hsc * (h0 + h1);
-                    betaz[u] = hsc * (h0 - h1);
-                } else {
-                    v0 = hsc * (f.x + m0v[i]);
-                }
-                float *tc = tile + kq * SR + r;
-                tc[0] = v0;
-                tc[SR] = hsc * (f.y + m1.w);
-                tc[2 * SR] = hsc * (f.z + m1.z);
-                tc[3 * SR] = hsc * (f.w + m1.y);
-            }
-        } else
+            for (int i = 0; i < U; ++i) stage(threadIdx.x + i * blockDim.x, x[i]);
+        } else {
 #pragma unroll 2
-        for (int q = threadIdx.x; q < units; q += blockDim.x) {
-            const int r = q >> (log2k - 2), kq = (q & (nq - 1)) << 2;
-            const int u = u0 + r, mu = (N - u) & (N - 1);
-            const int k = k0 + kq;
-            const float *Hu = hb + (size_t)u * M, *Hm = hb + (size_t)mu * M;
-            const float4 f = __ldcs(reinterpret_cast<const float4 *>(Hu + k));
-            const float4 m1 = __ldcs(reinterpret_cast<const float4 *>(Hm + (M - k - 4)));
-            const float m0 = k == 0 ? Hm[0] : __ldcs(Hm + (M - k));
-            float v0;
-            if (k == 0) {
-                const float h0 = 0.5f * (f.x + m0), h1 = 0.5f * (Hu[H2] + Hm[H2]);
-                v0 = hsc * (h0 + h1);
-                betaz[u] = hsc * (h0 - h1);
-            } else {
-                v0 = hsc * (f.x + m0);
-            }
-            float *tc = tile + kq * SR + r;
-            tc[0] = v0;
-            tc[SR] = hsc * (f.y + m1.w);
-            tc[2 * SR] = hsc * (f.z + m1.z);
-            tc[3 * SR] = hsc * (f.w + m1.y);
+            for (int q = threadIdx.x; q < units; q += blockDim.x) stage(q, load(q));
         }
     } else {
         const int n = R << log2k;
