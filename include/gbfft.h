@@ -339,10 +339,14 @@ int fft2_batched_plan_create(int count, const int64_t *rows, const int64_t *cols
 
 /* Run a batched plan: out_i = Re(ifft2(H_i . fft2(img_i))) for every image.
  * `images` is a DEVICE array of `count` gbfft_image_ptrs (caller-owned; the
- * kernels read it when they run).  Three persistent launches, one per stage
- * (forward rows, fused columns, inverse rows), each over a largest-first work
- * list of all images; with GBFFT_OPT_USE_GRAPH they are captured once in a
- * CUDA graph (on a private stream) and replayed on `stream`. */
+ * kernels read it when they run).  GBFFT_OPT_BATCH_FORM 0 (default): the
+ * one-shape kernels once per shape class over that class's images (filter
+ * preparations and the on-chip pipelines of sides <= 256 on a side stream);
+ * 1: four persistent launches (filter preparation, forward rows, fused
+ * columns, inverse rows), each over a largest-first work list of all
+ * images.  With GBFFT_OPT_USE_GRAPH (default on) the launches are captured
+ * once in a CUDA graph (on a private stream) and replayed on `stream`; the
+ * graph is captured again when `images` points elsewhere. */
 int fft2_filter_ifft2_batched(gbfft_plan_t plan, const gbfft_image_ptrs *images, gbfft_stream_t stream);
 
 /* Device buffers the autotuner runs a 1D or 2D plan on (host struct):
