@@ -441,6 +441,7 @@ def run_gbfft(args):
                              pipeline4096_column_forms=_guard(lambda: variant_column_forms(img, H, flush)),
                              pipeline4096_analytic_filter=_guard(lambda: variant_analytic(img, flush)),
                              pipeline4096_images_per_call=_guard(lambda: variant_images_per_call(img, H, flush)),
+                             pipeline4096_prepared_filter=_guard(lambda: variant_prepared_filter(img, H, flush)),
                              cufft_context=_guard(lambda: variant_cufft_context(img, H, ref, flush)))
             if args.variants else None,
             "alu_peaks_measured": _guard(lambda: {"fp64_fma_gflops": round(gb.measure_fma_peak(True) / 1e9, 1),
@@ -727,6 +728,25 @@ def variant_images_per_call(img, H, flush, steps: int = 30):
         del plan, x, out
         torch.cuda.empty_cache()
     return res
+
+
+def variant_prepared_filter(img, H, flush, steps: int = 100):
+    """The headline image with its filter prepared once (fft2_filter_prepare)
+    and every step running fft2_filter_ifft2_prepared: the serving form of a
+    fixed filter over a stream of images.  Not the headline (that prepares
+    its filter every step).  frac_algorithmic: the 26 B/px of the three
+    transform stages over the time, against the measured HBM bandwidth."""
+    import torch
+
+    import paper_cs_0103001_gb300 as gb
+
+    peak, _ = measured_peaks()
+    out = torch.empty_like(img)
+    plan = gb.Plan2D(img.shape[0], img.shape[1], 1, img.device)
+    plan.prepare_filter(H)
+    ms = _timed(lambda: plan.filter_prepared(img, out=out), steps, 5, flush)
+    return {"us": round(ms * 1e3, 2),
+            "frac_algorithmic": round(26 * img.numel() / (ms * 1e-3) / 1e9 / peak, 3)}
 
 
 def variant_paper_application(steps: int = 200):

@@ -213,6 +213,24 @@ int fft_inverse(gbfft_plan_t plan, const void *in, void *out, gbfft_stream_t str
  * so the call stays ordered on `stream` (and can be captured in a graph). */
 int fft2_filter_ifft2(gbfft_plan_t plan, const float *img, const float *H, float *out, gbfft_stream_t stream);
 
+/* The same pipeline with one filter for many calls (Sec. 5's filter, fixed
+ * while the images change, e.g. one PSF or low-pass over a stack of frames):
+ * fft2_filter_prepare computes the filter's prepared form (the even part
+ * s * Hs of the rows x cols real H, column-major, with the packed column's
+ * alpha and beta) into the plan's workspace on `stream`;
+ * fft2_filter_ifft2_prepared then runs the pipeline on `batch` images with
+ * it, without reading H and without the preparation: results equal
+ * fft2_filter_ifft2 with that H.  Needs a shared filter
+ * (GBFFT_OPT_H_BATCH_STRIDE 0, else GBFFT_ERR_UNSUPPORTED).  The prepared
+ * filter lives in the workspace region that fft2_filter_ifft2, _padded,
+ * _backward, fft2_spectrum and fft_plan_autotune also use: any of those
+ * calls, a new bind or an option that changes the workspace discards it, and
+ * fft2_filter_ifft2_prepared then returns GBFFT_ERR_INVALID_VALUE until the
+ * next fft2_filter_prepare.  Small sides (the on-chip path) run the
+ * three-pass kernels here. */
+int fft2_filter_prepare(gbfft_plan_t plan, const float *H, gbfft_stream_t stream);
+int fft2_filter_ifft2_prepared(gbfft_plan_t plan, const float *img, float *out, gbfft_stream_t stream);
+
 /* Sec. 5's application path for images whose sides are not powers of two:
  * each of the plan's `batch` images is in_rows x in_cols float32 (row-major,
  * contiguous, image b at img + b * in_rows * in_cols), 1 <= in_rows <= rows,

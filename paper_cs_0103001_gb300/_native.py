@@ -67,6 +67,8 @@ SIGNATURES = {
     "fft_forward": (_INT, [_P, _P, _P, _P]),
     "fft_inverse": (_INT, [_P, _P, _P, _P]),
     "fft2_filter_ifft2": (_INT, [_P, _P, _P, _P, _P]),
+    "fft2_filter_prepare": (_INT, [_P, _P, _P]),
+    "fft2_filter_ifft2_prepared": (_INT, [_P, _P, _P, _P]),
     "fft2_filter_ifft2_padded": (_INT, [_P, _P, _I64, _I64, _P, _P, _P]),
     "fft2_spectrum": (_INT, [_P, _P, _I64, _I64, _P, _P]),
     "fft2_filter_ifft2_analytic": (_INT, [_P, _P, _INT, ctypes.c_double, ctypes.c_double, _P, _P]),

@@ -159,6 +159,22 @@ class Plan2D(_PlanBase):
             nat.call("fft2_filter_ifft2", self.handle, _ptr(img), _ptr(H), _ptr(out), _stream_handle(img.device))
         return out
 
+    def prepare_filter(self, H: torch.Tensor) -> None:
+        """Prepare one filter for filter_prepared() calls (fft2_filter_prepare):
+        the filter of a stack of images, prepared once."""
+        _require_cuda(H, "H")
+        with self.lock:
+            nat.call("fft2_filter_prepare", self.handle, _ptr(H), _stream_handle(H.device))
+
+    def filter_prepared(self, img: torch.Tensor, out: torch.Tensor | None = None) -> torch.Tensor:
+        """filter() with the filter of the last prepare_filter()
+        (fft2_filter_ifft2_prepared; raises if it was discarded since)."""
+        if out is None:
+            out = torch.empty_like(img)
+        with self.lock:
+            nat.call("fft2_filter_ifft2_prepared", self.handle, _ptr(img), _ptr(out), _stream_handle(img.device))
+        return out
+
     def autotune(self, img: torch.Tensor, H: torch.Tensor, out: torch.Tensor | None = None) -> dict[str, int]:
         """Time the plan's candidate configurations on these buffers and keep
         the fastest (cached per GPU and shape); returns the chosen options."""

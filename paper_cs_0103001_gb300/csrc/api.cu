@@ -66,6 +66,7 @@ struct gbfft_plan {
     int nranks = 1, rank = 0;    // slab plans: the decomposition and this rank
     int fs_l1 = 0, fs_l2 = 0;    // four-step split
     bool fs3 = false;            // three passes of 256 (complex64, N = 2^24)
+    bool prepared = false;       // 2D: the workspace holds a filter of fft2_filter_prepare
     size_t off_tw6 = 0, off_tw7 = 0;  // three passes: the middle pass's two-level and coarse tables
     std::vector<ProfRec> prof;
     // guard bands: kAlign bytes of a fixed pattern after every workspace
@@ -181,6 +182,7 @@ bool fourstep3_applies(const gbfft_plan *p) {
 
 void layout(gbfft_plan *p) {
     size_t off = kAlign;  // a guard band before the first region
+    p->prepared = false;
     p->guards.assign(1, 0);
     if (p->kind == KIND_BATCH) {
         layout_batched(p);
@@ -693,6 +695,7 @@ int fft_plan_bind_workspace(gbfft_plan_t p, void *workspace, size_t bytes, gbfft
     p->ws = static_cast<char *>(workspace);
     p->ws_bytes = bytes;
     p->bound = false;
+    p->prepared = false;
     const bool dbl = is_dbl(p);
     int rc;
     {
@@ -773,8 +776,10 @@ int fft_inverse(gbfft_plan_t p, const void *in, void *out, gbfft_stream_t stream
 // row pass.
 // crop_r, crop_c > 0: img and out are crop_r x crop_c images in the top-left
 // corner of the plan's zero-padded grid (Sec. 5 application path).
+// use_prepared: the filter of fft2_filter_prepare, already in the workspace
+// (H unused; no preparation, and no on-chip path, which reads H itself).
 static int pipeline_chunk(gbfft_plan *p, const float *img, const float *H, float *out, int nb, bool first,
-                          cudaStream_t s, int crop_r = 0, int crop_c = 0) {
+                          cudaStream_t s, int crop_r = 0, int crop_c = 0, bool use_prepared = false) {
     const int rows = 1 << p->log2r, cols = 1 << p->log2c;
     const bool cropped = crop_r > 0;
     const int64_t half_px = (int64_t)rows * (cols / 2);
@@ -789,13 +794,14 @@ static int pipeline_chunk(gbfft_plan *p, const float *img, const float *H, float
     const int terms = (p->opt_precision == 1 || p->opt_precision == 2) ? (int)p->opt_precision + 1 : 0;
     const int tc5 = p->opt_precision >= 3 ? (int)p->opt_precision - 3 : -1;
     int *status = reinterpret_cast<int *>(p->ws + p->off_status);
-    if (!terms && tc5 < 0 && !cropped && p->opt_onchip && onchip_supported(rows, cols)) {
+    if (!use_prepared) p->prepared = false;  // every call with a filter of its own discards a prepared one
+    if (!use_prepared && !terms && tc5 < 0 && !cropped && p->opt_onchip && onchip_supported(rows, cols)) {
         return launch(p, GBFFT_STAGE_ONCHIP, s, [&] {
             return launch_onchip(img, H, out, p->opt_h_stride, rows, cols, nb, p->ws + p->off_tw0,
                                  p->ws + p->off_tw1, s);
         });
     }
-    const bool prep = per_image || first;  // a shared filter is prepared once per call
+    const bool prep = !use_prepared && (per_image || first);  // a shared filter is prepared once per call
     // with profiling on, the preparation runs on the caller's stream so that
     // every kernel's events time that kernel alone
     const bool side = prep && !p->opt_profile;
@@ -860,6 +866,43 @@ int fft2_filter_ifft2(gbfft_plan_t p, const float *img, const float *H, float *o
     for (int64_t b0 = 0; b0 < p->batch; b0 += p->chunk) {
         const int nb = (int)((p->batch - b0 < p->chunk) ? p->batch - b0 : p->chunk);
         rc = pipeline_chunk(p, img + b0 * np, H + b0 * p->opt_h_stride, out + b0 * np, nb, b0 == 0, s);
+        if (rc) return rc;
+    }
+    return GBFFT_OK;
+}
+
+int fft2_filter_prepare(gbfft_plan_t p, const float *H, gbfft_stream_t stream) {
+    int rc = check_plan_ready(p);
+    if (rc) return rc;
+    if (p->kind != KIND_2D) return GBFFT_ERR_INVALID_VALUE;
+    if (!H) return GBFFT_ERR_NULL;
+    if (misaligned(H)) return GBFFT_ERR_MISALIGNED;
+    if (p->opt_h_stride != 0) return GBFFT_ERR_UNSUPPORTED;  // one filter for every image
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int rows = 1 << p->log2r, cols = 1 << p->log2c;
+    const float scale = (float)(1.0 / ((double)rows * cols));
+    p->prepared = false;
+    rc = launch(p, GBFFT_STAGE_FILTER_PREP, s, [&] {
+        return launch_filter_prep(H, reinterpret_cast<float *>(p->ws + p->off_hs),
+                                  reinterpret_cast<float *>(p->ws + p->off_beta), rows, cols, 1, scale, 0, 0, 0, s);
+    });
+    if (rc) return rc;
+    p->prepared = true;
+    return GBFFT_OK;
+}
+
+int fft2_filter_ifft2_prepared(gbfft_plan_t p, const float *img, float *out, gbfft_stream_t stream) {
+    int rc = check_plan_ready(p);
+    if (rc) return rc;
+    if (p->kind != KIND_2D) return GBFFT_ERR_INVALID_VALUE;
+    if (!img || !out) return GBFFT_ERR_NULL;
+    if (misaligned(img) || misaligned(out)) return GBFFT_ERR_MISALIGNED;
+    if (!p->prepared) return GBFFT_ERR_INVALID_VALUE;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    const int64_t np = (int64_t)(1 << p->log2r) << p->log2c;
+    for (int64_t b0 = 0; b0 < p->batch; b0 += p->chunk) {
+        const int nb = (int)((p->batch - b0 < p->chunk) ? p->batch - b0 : p->chunk);
+        rc = pipeline_chunk(p, img + b0 * np, nullptr, out + b0 * np, nb, b0 == 0, s, 0, 0, true);
         if (rc) return rc;
     }
     return GBFFT_OK;
@@ -936,6 +979,7 @@ int fft2_spectrum(gbfft_plan_t p, const float *img, int64_t in_rows, int64_t in_
     // per-axis: F = DFT2 / (rows cols); Eq. 5: cols times that
     const float scale = (float)(p->opt_scale_conv ? 1.0 / rows : 1.0 / ((double)rows * cols));
     float *mag_T = reinterpret_cast<float *>(p->ws + p->off_hs);  // the prepared-filter area is scratch here
+    p->prepared = false;
     float *nyq = reinterpret_cast<float *>(p->ws + p->off_beta);
     const int64_t np = in_rows * in_cols;
     for (int64_t b0 = 0; b0 < p->batch; b0 += p->chunk) {
@@ -983,6 +1027,7 @@ int fft2_filter_ifft2_backward(gbfft_plan_t p, const float *img, const float *H,
     if (!p->opt_backward) return GBFFT_ERR_WORKSPACE;         // needs the second spectrum buffer
     void *spec_x = p->ws + p->off_buf, *spec_g = p->ws + p->off_buf2;
     float *hs = reinterpret_cast<float *>(p->ws + p->off_hs);
+    p->prepared = false;  // its own preparation overwrites the prepared filter
     float *beta = reinterpret_cast<float *>(p->ws + p->off_beta);
     float *grad_T = reinterpret_cast<float *>(p->ws + p->off_grad);
     const float scale = (float)(1.0 / (double)np);

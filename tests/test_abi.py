@@ -187,3 +187,16 @@ def test_corrupted_work_list_is_refused_before_the_gpu(nat):
     assert nat.lib.fft_plan_create(1024, 4, 1, ctypes.byref(h)) == nat.OK
     assert nat.lib.gbfft_selftest_corrupt_work_item(h, 0, 0, 0, 0) == nat.ERR_INVALID_VALUE
     assert nat.lib.fft_plan_destroy(h) == nat.OK
+
+
+def test_prepared_filter_entry_checks(nat):
+    """The prepared-filter calls refuse, before any CUDA call, a null plan
+    and an unbound one."""
+    buf = ctypes.c_void_p(256)
+    assert nat.lib.fft2_filter_prepare(None, buf, None) == nat.ERR_NULL
+    assert nat.lib.fft2_filter_ifft2_prepared(None, buf, buf, None) == nat.ERR_NULL
+    h = ctypes.c_void_p()
+    assert nat.lib.fft2_plan_create(256, 512, 1, 1, ctypes.byref(h)) == nat.OK
+    assert nat.lib.fft2_filter_prepare(h, buf, None) == nat.ERR_WORKSPACE
+    assert nat.lib.fft2_filter_ifft2_prepared(h, buf, buf, None) == nat.ERR_WORKSPACE
+    assert nat.lib.fft_plan_destroy(h) == nat.OK

@@ -177,3 +177,39 @@ def test_4096_filters_per_image_and_shared_over_chunks(gb, per_image, chunk):
     assert torch.equal(smem, glob)
     ref = oracle.pipeline(img, H)
     assert max_rel_l2(smem.cpu().numpy(), ref, axes=(1, 2)) <= tol_fp32(rows * cols)
+
+
+@pytest.mark.parametrize("rows,cols,batch,chunk", [(4096, 4096, 2, 0), (1024, 512, 5, 2), (256, 256, 3, 0)])
+def test_prepared_filter(gb, rows, cols, batch, chunk):
+    """One filter prepared once and used by later calls: equal to the plain
+    pipeline with that filter (bit for bit where both take the same kernels,
+    within the tolerance at 256^2, where the plain call takes the on-chip
+    path) and to the oracle; calls that reuse the workspace discard it."""
+    import ctypes
+
+    import torch
+
+    from paper_cs_0103001_gb300 import _native as nat
+
+    img = np.stack([synth.sky(rows, cols, 200, 20, b) for b in range(batch)])
+    H = synth.random_filter(rows, cols, 21)
+    H2 = synth.gaussian_lowpass(rows, cols, 30.0)
+    ti, th, th2 = torch.from_numpy(img).cuda(), torch.from_numpy(H).cuda(), torch.from_numpy(H2).cuda()
+    plan = gb.Plan2D(rows, cols, batch, "cuda", {nat.OPT_IMAGES_PER_CHUNK: chunk})
+    plan.prepare_filter(th)
+    a = plan.filter_prepared(ti)
+    b = plan.filter_prepared(ti)  # the prepared filter stays
+    assert torch.equal(a, b)
+    ref = oracle.pipeline(img, H)
+    assert max_rel_l2(a.cpu().numpy(), ref, axes=(1, 2)) <= tol_fp32(rows * cols)
+    plain = plan.filter(ti, th)  # discards the prepared filter
+    if rows > 256:
+        assert torch.equal(a, plain)
+    with pytest.raises(nat.GbfftError):
+        plan.filter_prepared(ti)
+    plan.prepare_filter(th2)
+    c = plan.filter_prepared(ti)
+    assert max_rel_l2(c.cpu().numpy(), oracle.pipeline(img, H2), axes=(1, 2)) <= tol_fp32(rows * cols)
+    # per-image filters: not this call's business
+    per = gb.Plan2D(rows, cols, batch, "cuda", {nat.OPT_H_BATCH_STRIDE: rows * cols})
+    assert nat.lib.fft2_filter_prepare(per.handle, ctypes.c_void_p(th.data_ptr()), None) == nat.ERR_UNSUPPORTED
