@@ -200,3 +200,27 @@ def test_prepared_filter_entry_checks(nat):
     assert nat.lib.fft2_filter_prepare(h, buf, None) == nat.ERR_WORKSPACE
     assert nat.lib.fft2_filter_ifft2_prepared(h, buf, buf, None) == nat.ERR_WORKSPACE
     assert nat.lib.fft_plan_destroy(h) == nat.OK
+
+
+def test_fourstep_passes_option(nat):
+    """GBFFT_OPT_FOURSTEP_PASSES: three passes by default for complex64 at
+    2^24 only; 2 or 3 accepted on 1D plans, other values and other plans
+    refused; the choice changes the workspace size."""
+    h = ctypes.c_void_p()
+    v = ctypes.c_int64()
+    ws2, ws3 = ctypes.c_size_t(), ctypes.c_size_t()
+    assert nat.lib.fft_plan_create(1 << 24, 2, nat.C64, ctypes.byref(h)) == nat.OK
+    assert nat.lib.fft_plan_get_option(h, nat.OPT_FOURSTEP_PASSES, ctypes.byref(v)) == nat.OK and v.value == 3
+    assert nat.lib.fft_plan_workspace_bytes(h, ctypes.byref(ws3)) == nat.OK
+    assert nat.lib.fft_plan_set_option(h, nat.OPT_FOURSTEP_PASSES, 2) == nat.OK
+    assert nat.lib.fft_plan_get_option(h, nat.OPT_FOURSTEP_PASSES, ctypes.byref(v)) == nat.OK and v.value == 2
+    assert nat.lib.fft_plan_workspace_bytes(h, ctypes.byref(ws2)) == nat.OK and ws2.value != ws3.value
+    assert nat.lib.fft_plan_set_option(h, nat.OPT_FOURSTEP_PASSES, 4) == nat.ERR_INVALID_VALUE
+    assert nat.lib.fft_plan_destroy(h) == nat.OK
+    for n, dt in ((1 << 20, nat.C64), (1 << 24, nat.C128)):
+        assert nat.lib.fft_plan_create(n, 1, dt, ctypes.byref(h)) == nat.OK
+        assert nat.lib.fft_plan_get_option(h, nat.OPT_FOURSTEP_PASSES, ctypes.byref(v)) == nat.OK and v.value == 2
+        assert nat.lib.fft_plan_destroy(h) == nat.OK
+    assert nat.lib.fft2_plan_create(256, 256, 1, 1, ctypes.byref(h)) == nat.OK
+    assert nat.lib.fft_plan_set_option(h, nat.OPT_FOURSTEP_PASSES, 3) == nat.ERR_INVALID_VALUE
+    assert nat.lib.fft_plan_destroy(h) == nat.OK
