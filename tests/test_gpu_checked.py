@@ -70,8 +70,16 @@ def exercise():
     assert rel_l2(mag, oracle.spectrum_padded(small, 512, 512)) <= tol_fp32(512 * 512)
     out = p.filter_analytic(t(synth.sky(512, 512, 50, 67)), nat.FILTER_GAUSSIAN, 20.0)
     plans.append(p)
-    # 1D: one-pass, four-step, cluster
-    for n, batch, onchip in ((4096, 8, 1), (1 << 20, 2, 1), (1 << 16, 4, 2)):
+    # the prepared filter
+    img = np.stack([synth.sky(1024, 512, 40, 69, b) for b in range(2)])
+    H = synth.random_filter(1024, 512, 70)
+    p = gb.Plan2D(1024, 512, 2, "cuda")
+    p.prepare_filter(t(H))
+    out = p.filter_prepared(t(img)).cpu().numpy()
+    assert max_rel_l2(out, oracle.pipeline(img, H), axes=(1, 2)) <= tol_fp32(1024 * 512)
+    plans.append(p)
+    # 1D: one-pass, four-step, cluster, three passes of 256 (2^24)
+    for n, batch, onchip in ((4096, 8, 1), (1 << 20, 2, 1), (1 << 16, 4, 2), (1 << 24, 1, 1)):
         x = synth.complex_uniform((batch, n), 68, n)
         p = gb.Plan1D(n, batch, torch.complex64, "cuda", {nat.OPT_ONCHIP: onchip})
         y = p.forward(t(x)).cpu().numpy()
