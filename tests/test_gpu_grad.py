@@ -123,3 +123,32 @@ def test_backward_differentiable_workload_size(gb):
                 for b in range(batch))
     print(f"grad_H DC error {abs(gh[0, 0] - gh_ref[0, 0]):.3e} (bound {2 * bound:.3e})")
     assert abs(gh[0, 0] - gh_ref[0, 0]) <= 2 * bound
+
+
+def test_filter_gradient_of_a_split_batch_is_the_sum_of_the_shards():
+    """Data-parallel adjoint on one GPU: grad_H of a batch of 4 equals the
+    sum of the grad_H of its two halves (what one all-reduce over two ranks
+    forms), within the fp32 bound, and matches the oracle."""
+    import torch
+
+    import paper_cs_0103001_gb300 as gb
+    from paper_cs_0103001_gb300 import _native as nat
+
+    B, rows, cols = 4, 256, 512
+    img = np.stack([synth.sky(rows, cols, 30, 80, b) for b in range(B)])
+    G = synth.real_uniform((B, rows, cols), 81)
+    H = synth.random_filter(rows, cols, 82)
+
+    def grad_H(lo, hi):
+        p = gb.Plan2D(rows, cols, hi - lo, "cuda", {nat.OPT_ENABLE_BACKWARD: 1})
+        gi = torch.empty(hi - lo, rows, cols, device="cuda")
+        gh = torch.empty(rows, cols, device="cuda")
+        p.backward(torch.from_numpy(img[lo:hi]).cuda(), torch.from_numpy(H).cuda(),
+                   torch.from_numpy(G[lo:hi]).cuda(), gi, gh)
+        return gh.cpu().numpy().astype(np.float64)
+
+    whole = grad_H(0, B)
+    summed = grad_H(0, 2) + grad_H(2, B)
+    _, ref = oracle.pipeline_grad(img, H, G)
+    assert rel_l2(summed, whole) <= 1e-6
+    assert rel_l2(summed, ref) <= 1e-5
