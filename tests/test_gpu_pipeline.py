@@ -213,3 +213,13 @@ def test_prepared_filter(gb, rows, cols, batch, chunk):
     # per-image filters: not this call's business
     per = gb.Plan2D(rows, cols, batch, "cuda", {nat.OPT_H_BATCH_STRIDE: rows * cols})
     assert nat.lib.fft2_filter_prepare(per.handle, ctypes.c_void_p(th.data_ptr()), None) == nat.ERR_UNSUPPORTED
+
+
+def test_largest_image_8192_squared(gb):
+    """The largest 2D plan, 8192 x 8192 (rows of 8192: 1024-thread row
+    blocks; columns of 8192: one column per block), with an asymmetric
+    filter, against the oracle."""
+    rows = cols = 8192
+    img = synth.sky(rows, cols, 20000, 22)
+    H = synth.random_filter(rows, cols, 23)
+    assert rel_l2(_pipe(gb, img, H), oracle.pipeline(img, H)) <= tol_fp32(rows * cols)
