@@ -442,6 +442,7 @@ def run_gbfft(args):
                              pipeline4096_analytic_filter=_guard(lambda: variant_analytic(img, flush)),
                              pipeline4096_images_per_call=_guard(lambda: variant_images_per_call(img, H, flush)),
                              pipeline4096_prepared_filter=_guard(lambda: variant_prepared_filter(img, H, flush)),
+                             pipeline4096_unflushed=_guard(lambda: variant_unflushed(img, H)),
                              cufft_context=_guard(lambda: variant_cufft_context(img, H, ref, flush)))
             if args.variants else None,
             "alu_peaks_measured": _guard(lambda: {"fp64_fma_gflops": round(gb.measure_fma_peak(True) / 1e9, 1),
@@ -691,6 +692,45 @@ def variant_analytic(img, flush, steps: int = 100):
     ms = _timed(lambda: plan.filter_analytic(img, nat.FILTER_BUTTERWORTH, 4, d0, out=out), steps, 5, flush)
     return {"us": round(ms * 1e3, 2), "gbs_44Bpx": round(METRIC_BYTES_PER_PX * ROWS * COLS / (ms * 1e-3) / 1e9, 1),
             "filter": "butterworth order 4, D0 = 0.1 Nyquist, by formula"}
+
+
+def variant_unflushed(img, H, steps: int = 200):
+    """The headline step back to back with no L2 flush between steps, cycling
+    over four distinct (image, filter, output) sets: 768 MiB of inputs and
+    outputs, six times the L2, so no step finds its own data there.  The
+    headline writes a 256 MiB buffer before every step instead, and its
+    step then also pays for writing that buffer's dirty L2 lines back to
+    HBM; this is the rate of a stream of images.  Time per step from events
+    around the whole run (one synchronisation), and frac_algorithmic on the
+    schedule's 32 B/px."""
+    import torch
+
+    import paper_cs_0103001_gb300 as gb
+
+    peak, _ = measured_peaks()
+    sets = []
+    for j in range(4):
+        x = img * (1.0 + 0.01 * j)  # distinct buffers (and values)
+        h = H * (1.0 - 0.01 * j)
+        sets.append((x, h, torch.empty_like(img)))
+    plan = gb.Plan2D(img.shape[0], img.shape[1], 1, img.device)
+    for j in range(8):
+        x, h, o = sets[j & 3]
+        plan.filter(x, h, out=o)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record()
+    for j in range(steps):
+        x, h, o = sets[j & 3]
+        plan.filter(x, h, out=o)
+    b.record()
+    b.synchronize()
+    us = a.elapsed_time(b) * 1e3 / steps
+    del plan, sets
+    torch.cuda.empty_cache()
+    return {"us_per_image": round(us, 1), "steps": steps, "input_sets": 4,
+            "frac_algorithmic": round(32 * img.numel() / (us * 1e-6) / 1e9 / peak, 3)}
 
 
 def variant_images_per_call(img, H, flush, steps: int = 30):
