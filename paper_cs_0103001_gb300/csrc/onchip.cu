@@ -29,9 +29,13 @@ namespace cg = cooperative_groups;
 
 namespace gbfft {
 
-template <int R, int M> struct OnChipCfg {
+// WIDE: 8 row pairs per CTA and up to 16 CTAs per cluster (a size beyond the
+// portable 8, allowed per kernel), for one or a few images: half the work of
+// each SM, on twice the SMs.
+template <int R, int M, bool WIDE = false> struct OnChipCfg {
     static constexpr int E = 16;
-    static constexpr int C = R / 32 < 1 ? 1 : (R / 32 > 8 ? 8 : R / 32);  // CTAs per cluster (16 pairs each)
+    static constexpr int RPC = WIDE ? 16 : 32, CMAX = WIDE ? 16 : 8;  // rows per CTA, largest cluster
+    static constexpr int C = R / RPC < 1 ? 1 : (R / RPC > CMAX ? CMAX : R / RPC);  // CTAs per cluster
     static constexpr int PP = R / (2 * C);                                 // row pairs per CTA
     static constexpr int KC = (M / 2) / C;                                 // half-spectrum columns per CTA
     static constexpr int TR = M / E, TC = R / E;                           // threads per row / column FFT
@@ -57,11 +61,14 @@ template <int R, int PP> __device__ __forceinline__ void owner_of(int u, int &ct
     slot = side * PP + (p % PP);
 }
 
-template <int R, int M>
-__global__ void __launch_bounds__(OnChipCfg<R, M>::THREADS)
+// the wide form's split exists (every CTA gets at least one half-spectrum column)
+template <int R, int M> constexpr bool onchip_wide_ok() { return R >= 128 && M / 2 >= (R / 16 > 16 ? 16 : R / 16); }
+
+template <int R, int M, bool WIDE>
+__global__ void __launch_bounds__(OnChipCfg<R, M, WIDE>::THREADS)
     k_onchip(const float *__restrict__ img, const float *__restrict__ H, float *__restrict__ out, long long h_stride,
              float scale, const float2 *__restrict__ twm, const float2 *__restrict__ twr, ImgIndirect ind) {
-    typedef OnChipCfg<R, M> K;
+    typedef OnChipCfg<R, M, WIDE> K;
     constexpr int E = K::E, PP = K::PP, SRS = K::SRS, H2 = M / 2;
     extern __shared__ __align__(16) unsigned char smraw[];
     float2 *spec = reinterpret_cast<float2 *>(smraw);
@@ -256,12 +263,13 @@ __global__ void __launch_bounds__(OnChipCfg<R, M>::THREADS)
     }
 }
 
-template <int R, int M>
+template <int R, int M, bool WIDE>
 static cudaError_t onchip_launch(const float *img, const float *H, float *out, long long h_stride, int nimg,
                                  const void *twm, const void *twr, cudaStream_t s, ImgIndirect ind) {
-    typedef OnChipCfg<R, M> K;
-    const void *kern = (const void *)k_onchip<R, M>;
+    typedef OnChipCfg<R, M, WIDE> K;
+    const void *kern = (const void *)k_onchip<R, M, WIDE>;
     cudaError_t e = set_smem_attrs(kern, K::SMEM);
+    if (e == cudaSuccess && K::C > 8) e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     if (e != cudaSuccess) return e;
     const float scale = (float)(1.0 / ((double)R * M));
     for (int z0 = 0; z0 < nimg; z0 += 65535) {
@@ -279,12 +287,55 @@ static cudaError_t onchip_launch(const float *img, const float *H, float *out, l
         cfg.attrs = at;
         cfg.numAttrs = 1;
         const ImgIndirect iz{ind.ptrs, ind.ptrs ? ind.idx + z0 : nullptr};
-        e = cudaLaunchKernelEx(&cfg, k_onchip<R, M>, ind.ptrs ? img : img + (size_t)z0 * R * M,
+        e = cudaLaunchKernelEx(&cfg, k_onchip<R, M, WIDE>, ind.ptrs ? img : img + (size_t)z0 * R * M,
                                ind.ptrs ? H : H + (size_t)z0 * h_stride, ind.ptrs ? out : out + (size_t)z0 * R * M,
                                h_stride, scale, static_cast<const float2 *>(twm), static_cast<const float2 *>(twr), iz);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+}
+
+// The wide form where it exists, when nimg images of it fit the GPU's SMs at
+// once and a cluster of its size can be resident (checked once per shape).
+template <int R, int M>
+static cudaError_t onchip_dispatch(const float *img, const float *H, float *out, long long h_stride, int nimg,
+                                   const void *twm, const void *twr, cudaStream_t s, ImgIndirect ind) {
+    if constexpr (onchip_wide_ok<R, M>()) {
+        typedef OnChipCfg<R, M, true> K;
+        static int wide = -1;  // per process (one device type): 1 if the wide cluster can be resident
+        static int sms = 0;
+        if (wide < 0) {
+            const void *kern = (const void *)k_onchip<R, M, true>;
+            int dev = 0, n = 0;
+            cudaError_t e = set_smem_attrs(kern, K::SMEM);
+            if (e == cudaSuccess && K::C > 8)
+                e = cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+            if (e == cudaSuccess) e = cudaGetDevice(&dev);
+            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            if (e == cudaSuccess) {
+                cudaLaunchConfig_t cfg = {};
+                cfg.gridDim = dim3(K::C, 1, 1);
+                cfg.blockDim = dim3(K::THREADS, 1, 1);
+                cfg.dynamicSmemBytes = K::SMEM;
+                cudaLaunchAttribute at[1];
+                at[0].id = cudaLaunchAttributeClusterDimension;
+                at[0].val.clusterDim.x = K::C;
+                at[0].val.clusterDim.y = 1;
+                at[0].val.clusterDim.z = 1;
+                cfg.attrs = at;
+                cfg.numAttrs = 1;
+                e = cudaOccupancyMaxActiveClusters(&n, k_onchip<R, M, true>, &cfg);
+            }
+            if (e != cudaSuccess) {
+                (void)cudaGetLastError();  // a refused query only means: not the wide form
+                n = 0;
+            }
+            wide = n > 0 ? 1 : 0;
+        }
+        if (wide == 1 && (long long)nimg * K::C <= sms)
+            return onchip_launch<R, M, true>(img, H, out, h_stride, nimg, twm, twr, s, ind);
+    }
+    return onchip_launch<R, M, false>(img, H, out, h_stride, nimg, twm, twr, s, ind);
 }
 
 bool onchip_supported(int rows, int cols) { return rows >= 16 && rows <= 256 && cols >= 16 && cols <= 256; }
@@ -298,7 +349,7 @@ cudaError_t launch_onchip(const float *img, const float *H, float *out, long lon
     switch (ilog2(rows) * 16 + ilog2(cols)) {
 #define GBFFT_C(LR, LC) \
     case LR * 16 + LC:                                                                                         \
-        return onchip_launch<(1 << LR), (1 << LC)>(img, H, out, h_stride, nimg, tw_cols, tw_rows, s, ind);
+        return onchip_dispatch<(1 << LR), (1 << LC)>(img, H, out, h_stride, nimg, tw_cols, tw_rows, s, ind);
         GBFFT_OC_ALL(GBFFT_C)
 #undef GBFFT_C
         default: return cudaErrorInvalidValue;
