@@ -68,6 +68,25 @@ def test_per_image_filters_many_clusters(gb):
     assert max_rel_l2(out, oracle.pipeline(img, H), axes=(1, 2)) <= tol_fp32(rows * cols)
 
 
+@pytest.mark.parametrize("rows,cols", [(256, 256), (128, 64)])
+def test_wide_and_portable_clusters(gb, rows, cols):
+    """One image of 128 or 256 rows runs on the wide clusters (16 rows per
+    CTA, up to 16 CTAs); 20 images do not fit the GPU's SMs that way and run
+    on the portable ones (32 rows per CTA).  Both give the oracle's result
+    for the same image."""
+    B = 20
+    img = np.stack([synth.sky(rows, cols, 40, 47, b) for b in range(B)])
+    H = synth.random_filter(rows, cols, 48)
+    ref = oracle.pipeline(img, H)
+    tol = tol_fp32(rows * cols)
+    one, prof1 = _run(gb, img[:1], H, 1)
+    many, prof_b = _run(gb, img, H, 1)
+    assert prof1["onchip"][1] == 1 and prof_b["onchip"][1] == 1
+    assert rel_l2(one[0], ref[0]) <= tol
+    assert max_rel_l2(many, ref, axes=(1, 2)) <= tol
+    assert rel_l2(one[0], many[0]) <= 2 * tol
+
+
 def test_workload_256_gaussian32(gb):
     """The 256^2 sky (50 sources) with the sigma = 32 Gaussian low-pass."""
     img = synth.sky(256, 256, 50, 0)[None]
