@@ -304,6 +304,13 @@ static cudaError_t onchip_dispatch(const float *img, const float *H, float *out,
         typedef OnChipCfg<R, M, true> K;
         static int wide = -1;  // per process (one device type): 1 if the wide cluster can be resident
         static int sms = 0;
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        if (wide < 0 && (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)) {
+            (void)cudaGetLastError();
+            // the first call of this shape is being captured: the portable form,
+            // with no device queries inside the capture
+            return onchip_launch<R, M, false>(img, H, out, h_stride, nimg, twm, twr, s, ind);
+        }
         if (wide < 0) {
             const void *kern = (const void *)k_onchip<R, M, true>;
             int dev = 0, n = 0;

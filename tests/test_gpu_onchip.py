@@ -2,6 +2,10 @@
 thread-block cluster per image, half spectra in shared memory) against the
 FP64 oracle and against the three-pass path, through the C ABI."""
 
+import os
+import subprocess
+import sys
+
 import numpy as np
 import pytest
 
@@ -141,3 +145,43 @@ def test_graph_capture_replay(gb, rows, cols):
     g.replay()
     torch.cuda.synchronize()
     assert rel_l2(out.cpu().numpy(), oracle.pipeline(img2, H2)) <= tol_fp32(rows * cols)
+
+
+FIRST_CALL_CAPTURED = r'''
+import numpy as np, torch
+import oracle
+import paper_cs_0103001_gb300 as gb
+from paper_cs_0103001_gb300 import synth
+from tests.gpu_util import rel_l2, tol_fp32
+rows, cols = 256, 128
+plan = gb.Plan2D(rows, cols, 1, "cuda")
+img = torch.from_numpy(synth.sky(rows, cols, 20, 49)).cuda()
+H = torch.from_numpy(synth.random_filter(rows, cols, 50)).cuda()
+out = torch.empty_like(img)
+s = torch.cuda.Stream()
+s.wait_stream(torch.cuda.current_stream())
+g = torch.cuda.CUDAGraph()
+with torch.cuda.graph(g, stream=s):
+    plan.filter(img, H, out=out)
+g.replay()
+torch.cuda.synchronize()
+ref = oracle.pipeline(img.cpu().numpy(), H.cpu().numpy())
+assert rel_l2(out.cpu().numpy(), ref) <= tol_fp32(rows * cols)
+out2 = plan.filter(img, H)
+torch.cuda.synchronize()
+assert rel_l2(out2.cpu().numpy(), ref) <= tol_fp32(rows * cols)
+print("first call captured: ok")
+'''
+
+
+def test_first_call_of_a_shape_inside_graph_capture():
+    """The first call of a shape that could take the wide clusters, made
+    inside a CUDA graph capture (a fresh process, so nothing of the shape was
+    set up before): it is captured on the portable clusters with no device
+    query in the capture, the replay gives the oracle's result, and a later
+    eager call (which sets up the wide form) does too."""
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", FIRST_CALL_CAPTURED], cwd=root, capture_output=True, text=True,
+                       timeout=600)
+    print(r.stdout[-2000:], r.stderr[-4000:])
+    assert r.returncode == 0 and "first call captured: ok" in r.stdout
